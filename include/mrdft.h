@@ -1,0 +1,135 @@
+/*
+ * mrdft.h -- C ABI of the GB300 (sm_103a) multiresolution DFT library.
+ *
+ * The transform (Andreatto & Cariow, "An algorithm for fast computation of
+ * the multiresolution discrete Fourier transform", arXiv:1507.02525):
+ * Sec. 2, Eq. 1 -- for a signal x of length N = 2^m (m >= 1) and every level
+ * i = 1..m, the unnormalised spectra of the N/2^i non-overlapping rectangular
+ * windows of length 2^i:
+ *
+ *     Y^(i)[w 2^i + k] = sum_{n=0}^{2^i - 1} x[w 2^i + n] exp(-j 2 pi n k / 2^i)
+ *
+ * computed with the level recursion of Sec. 3 (Eq. 4: even bins are the sum of
+ * the two child spectra, odd bins a DFT of the twiddled half-difference).
+ * Output order: levels ascending, windows ascending, bins natural (the
+ * permutation Gamma of Sec. 3 applied).  Complex values are complex64:
+ * interleaved (re, im) IEEE single precision.
+ *
+ * Layout of a plan's data (a batch of S signals, lengths N_s = 2^{m_s}):
+ *   x : signals concatenated, signal s starting at sample sum_{t<s} N_t;
+ *       complex64 (MRDFT_C64) or float32 (MRDFT_R32, promoted to complex
+ *       with zero imaginary part).
+ *   y : complex64, signal s starting at sum_{t<s} m_t N_t; inside a signal
+ *       level i (1-based) occupies [ (i-1) N_s, i N_s ).
+ *   gy: same layout as y.   gx: complex64, same layout as x.
+ * All buffers are DEVICE pointers, owned by the caller, 16-byte aligned, and
+ * must not alias one another.  Work is asynchronous on the given stream.
+ *
+ * Errors: every call returns an mrdft_status; nothing throws across the ABI.
+ * A failed call leaves a message retrievable with mrdft_last_error().
+ * Kernels report asynchronous faults (a wait that gave up, an invalid work
+ * item) in a device status word read back by mrdft_status_poll().
+ */
+#ifndef MRDFT_H_
+#define MRDFT_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mrdft_plan_s* mrdft_plan_t;
+typedef struct CUstream_st* mrdft_stream_t; /* a cudaStream_t; NULL = legacy default stream */
+
+typedef enum {
+  MRDFT_OK = 0,
+  MRDFT_EINVAL = 1,       /* bad argument: length not a power of two, null pointer, ... */
+  MRDFT_ENOMEM = 2,       /* device or host allocation failed */
+  MRDFT_ECUDA = 3,        /* a CUDA runtime call failed (message in mrdft_last_error) */
+  MRDFT_EUNSUPPORTED = 4, /* valid request the library does not implement */
+  MRDFT_ETIMEOUT = 5,     /* a device-side wait gave up (reported by mrdft_status_poll) */
+  MRDFT_EDEVICE = 6       /* a kernel flagged an invalid work item (mrdft_status_poll) */
+} mrdft_status;
+
+typedef enum {
+  MRDFT_C64 = 0, /* complex64 input */
+  MRDFT_R32 = 1  /* real float32 input, complex64 output */
+} mrdft_dtype;
+
+/* Plan flags. */
+#define MRDFT_FLAG_GRAPH 1u /* replay a CUDA graph of the launch sequence (captured
+                               on the first call for each (input, output) pair) */
+
+/*
+ * mrdft_plan -- validate the signal lengths and allocate everything a
+ * transform needs on the current CUDA device: twiddle tables (FP64 values
+ * rounded once to FP32), work lists, scratch.
+ *   out       : receives the plan (set to NULL on failure).
+ *   lengths   : host array of n_lengths signal lengths; each a power of two
+ *               in [2, 2^26] (m in 1..26).
+ *   n_lengths : 1 -> `batch` signals of length lengths[0] (uniform batch);
+ *               == batch -> one length per signal (ragged batch).
+ *   batch     : number of signals, >= 1.
+ *   dtype     : MRDFT_C64 or MRDFT_R32 input.
+ *   flags     : MRDFT_FLAG_* bits.
+ * Returns MRDFT_EINVAL for a bad length or count, MRDFT_ENOMEM / MRDFT_ECUDA
+ * when allocation fails.  The plan is bound to the device current at the
+ * call; it may be used from one stream at a time.
+ */
+mrdft_status mrdft_plan(mrdft_plan_t* out, const int64_t* lengths, int64_t n_lengths,
+                        int64_t batch, int dtype, uint32_t flags);
+
+/* Total complex outputs of the plan, sum_s m_s N_s (the length of y and gy). */
+mrdft_status mrdft_output_elems(mrdft_plan_t plan, int64_t* elems);
+
+/* Total input samples of the plan, sum_s N_s (the length of x and gx). */
+mrdft_status mrdft_input_elems(mrdft_plan_t plan, int64_t* elems);
+
+/*
+ * mrdft_forward -- Eq. 1 for every signal of the plan (Sec. 3 recursion).
+ *   x : device input (layout above), y : device output, stream : CUDA stream.
+ * Asynchronous; returns MRDFT_EINVAL for null or misaligned pointers.
+ */
+mrdft_status mrdft_forward(mrdft_plan_t plan, const void* x, void* y, mrdft_stream_t stream);
+
+/*
+ * mrdft_adjoint -- the conjugate transpose of Eq. 1,
+ *   gx = sum_i (I_{N/2^i} (x) E_{2^i})^H gy_i   (unnormalised inverse DFT per
+ * window, summed over levels), the reverse of the Sec. 3 recursion.
+ *   gy : device complex64 gradient with the layout of y;
+ *   gx : device complex64 result with the layout of x (for MRDFT_R32 plans the
+ *        gradient with respect to the real input is Re(gx)).
+ */
+mrdft_status mrdft_adjoint(mrdft_plan_t plan, const void* gy, void* gx, mrdft_stream_t stream);
+
+/*
+ * mrdft_forward_host -- the same transform for HOST buffers: copies x to the
+ * plan's device staging buffers on `stream`, runs mrdft_forward, copies y
+ * back and synchronises the stream.  x and y are host pointers (pinned
+ * memory gives full copy bandwidth).  The first call allocates the staging
+ * buffers (MRDFT_ENOMEM on failure).
+ */
+mrdft_status mrdft_forward_host(mrdft_plan_t plan, const void* x_host, void* y_host,
+                                mrdft_stream_t stream);
+
+/* Read and clear the device status word; waits for the plan's last work. */
+mrdft_status mrdft_status_poll(mrdft_plan_t plan);
+
+/* Message of the last failed call on this plan (or of the last failed
+ * mrdft_plan when plan is NULL).  Never NULL. */
+const char* mrdft_last_error(mrdft_plan_t plan);
+
+/* Launch configuration the plan picked: tile log2 size and the number of
+ * kernel launches one forward / adjoint issues. */
+mrdft_status mrdft_plan_info(mrdft_plan_t plan, int32_t* tile_log, int32_t* fwd_launches,
+                             int32_t* adj_launches);
+
+/* Release everything the plan owns.  NULL is ignored. */
+void mrdft_destroy(mrdft_plan_t plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MRDFT_H_ */

@@ -1,0 +1,147 @@
+"""ctypes binding of the C ABI in ``include/mrdft.h`` (argument marshalling only).
+
+Every step of the transform runs in the CUDA library; this module only
+passes device pointers, sizes and stream handles.  Loading fails loudly when
+``libmrdft.so`` is missing: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libmrdft.so")
+
+MRDFT_OK = 0
+MRDFT_EINVAL = 1
+MRDFT_ENOMEM = 2
+MRDFT_ECUDA = 3
+MRDFT_EUNSUPPORTED = 4
+MRDFT_ETIMEOUT = 5
+MRDFT_EDEVICE = 6
+MRDFT_C64 = 0
+MRDFT_R32 = 1
+MRDFT_FLAG_GRAPH = 1
+
+STATUS_NAMES = {0: "MRDFT_OK", 1: "MRDFT_EINVAL", 2: "MRDFT_ENOMEM", 3: "MRDFT_ECUDA",
+                4: "MRDFT_EUNSUPPORTED", 5: "MRDFT_ETIMEOUT", 6: "MRDFT_EDEVICE"}
+
+# every entry point declared in include/mrdft.h
+EXPORTS = ("mrdft_plan", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
+           "mrdft_adjoint", "mrdft_forward_host", "mrdft_status_poll", "mrdft_last_error",
+           "mrdft_plan_info", "mrdft_destroy")
+
+
+class MrdftError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libmrdft.so (building it from source first if it is absent or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if build_if_missing:
+            from . import build as _build
+            if _build.is_stale():
+                _build.build()
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"MrDFT CUDA library not found at {LIB_PATH}; "
+                               "run paper_1507_02525_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32
+        lib.mrdft_plan.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), i64, i64, i32, u32]
+        lib.mrdft_output_elems.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.mrdft_input_elems.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.mrdft_forward.argtypes = [vp, vp, vp, vp]
+        lib.mrdft_adjoint.argtypes = [vp, vp, vp, vp]
+        lib.mrdft_forward_host.argtypes = [vp, vp, vp, vp]
+        lib.mrdft_status_poll.argtypes = [vp]
+        lib.mrdft_last_error.argtypes = [vp]
+        lib.mrdft_last_error.restype = ctypes.c_char_p
+        lib.mrdft_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
+                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        lib.mrdft_destroy.argtypes = [vp]
+        lib.mrdft_destroy.restype = None
+        for name in ("mrdft_plan", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
+                     "mrdft_adjoint", "mrdft_forward_host", "mrdft_status_poll", "mrdft_plan_info"):
+            getattr(lib, name).restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+def check(status: int, plan=None) -> None:
+    if status != MRDFT_OK:
+        msg = load().mrdft_last_error(plan).decode(errors="replace")
+        raise MrdftError(status, msg)
+
+
+class Plan:
+    """Owner of an ``mrdft_plan_t`` (see ``mrdft_plan`` in include/mrdft.h)."""
+
+    def __init__(self, lengths, batch: int | None = None, real_input: bool = False,
+                 graph: bool = False):
+        lib = load()
+        lengths = [int(v) for v in (lengths if hasattr(lengths, "__len__") else [lengths])]
+        if batch is None:
+            batch = len(lengths)
+        arr = (ctypes.c_int64 * len(lengths))(*lengths)
+        h = ctypes.c_void_p()
+        st = lib.mrdft_plan(ctypes.byref(h), arr, len(lengths), int(batch),
+                            MRDFT_R32 if real_input else MRDFT_C64,
+                            MRDFT_FLAG_GRAPH if graph else 0)
+        check(st, None)
+        self._h = h
+        self._lib = lib
+        self.batch = int(batch)
+        self.lengths = lengths if len(lengths) == batch else lengths * batch
+        self.real_input = real_input
+        self.graph = graph
+        n = ctypes.c_int64()
+        check(lib.mrdft_output_elems(h, ctypes.byref(n)), h)
+        self.out_elems = n.value
+        check(lib.mrdft_input_elems(h, ctypes.byref(n)), h)
+        self.in_elems = n.value
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(self._lib.mrdft_plan_info(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), self._h)
+        return {"tile_log": a.value, "fwd_launches": b.value, "adj_launches": c.value}
+
+    def forward(self, x_ptr: int, y_ptr: int, stream: int = 0) -> None:
+        check(self._lib.mrdft_forward(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr),
+                                      ctypes.c_void_p(stream)), self._h)
+
+    def adjoint(self, gy_ptr: int, gx_ptr: int, stream: int = 0) -> None:
+        check(self._lib.mrdft_adjoint(self._h, ctypes.c_void_p(gy_ptr), ctypes.c_void_p(gx_ptr),
+                                      ctypes.c_void_p(stream)), self._h)
+
+    def forward_host(self, x_host_ptr: int, y_host_ptr: int, stream: int = 0) -> None:
+        check(self._lib.mrdft_forward_host(self._h, ctypes.c_void_p(x_host_ptr),
+                                           ctypes.c_void_p(y_host_ptr), ctypes.c_void_p(stream)), self._h)
+
+    def status_poll(self) -> None:
+        check(self._lib.mrdft_status_poll(self._h), self._h)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.mrdft_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

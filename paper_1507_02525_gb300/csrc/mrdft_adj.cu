@@ -1,0 +1,405 @@
+// Adjoint MrDFT kernels (sm_103a): x_bar = sum_i (I (x) E_{2^i})^H g_i, the
+// conjugate transpose of Eq. 1, taken as the transpose of the level recursion
+// of Sec. 3 (Eq. 4) run from the top level down.  For a window at level i with
+// accumulated gradient G_i (upstream g_i plus what its parent passed down):
+//   even bins: both children receive G_i[2k] at their bin k         (U^T)
+//   odd bins : zb = IDFT_h(G_i[2k+1]) (unnormalised), then
+//              a_bar[n] += conj(w_{2^i}^n) zb[n], b_bar[n] -= the same (V^T D^H)
+//   level 1  : x_bar[2w] += G[0] + G[1], x_bar[2w+1] += G[0] - G[1]   (A^(1)T)
+// The inverse DFTs use the forward engine on conjugated data.
+//
+//   k_adj_window / k_adj_rows + k_adj_cols : levels above the tile, top down;
+//     even-bin propagation to the next level in `e_out` (N/2 per signal),
+//     time-domain contributions accumulated in `acc` (N per signal).
+//   k_adj_tile : levels tlog..1 of a tile, adds `acc`, writes x_bar.
+#include <cuda_runtime.h>
+
+#include "mrdft_fft.cuh"
+#include "mrdft_internal.h"
+
+namespace mrdft {
+
+__device__ __forceinline__ float4 ld4s_a(const float2* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ void st4s_a(float2* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ float2 conjf2(float2 v) { return make_float2(v.x, -v.y); }
+
+// ===================================================================== tile
+
+struct AdjTileSig {
+  int64_t x_base;    // gx / acc offset of the tile's first sample
+  int64_t g_base;    // gy offset of the tile's first level-1 bin
+  int32_t m;
+  int32_t pad;
+};
+constexpr int kAdjMaxPack = kTile / 32;
+
+// Levels 4..1 of one 16-position chunk (a level-4 window) in registers.
+// P = the level-5 parent's even bins for this window, acc = x_bar so far.
+__device__ __forceinline__ void adj_chunk_levels_4_1(const AdjArgs& a, const AdjTileSig& ts, int off,
+                                                     float2 (&P)[16], float2 (&acc)[16]) {
+  const float2* gl = a.gy + ts.g_base + off;
+  const int64_t lstride = (int64_t)1 << ts.m;
+  static_for<0, 4>([&](auto JJ) MRDFT_INL {
+    constexpr int j = 4 - decltype(JJ)::value;  // 4, 3, 2, 1
+    constexpr int L = 1 << j, h = L / 2;
+    float2 G[16], Pn[8];
+    const float4* g4 = reinterpret_cast<const float4*>(gl + (j - 1) * lstride);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const float4 v = __ldcs(g4 + q);
+      G[2 * q] = make_float2(v.x, v.y);
+      G[2 * q + 1] = make_float2(v.z, v.w);
+    }
+    static_for<0, 16 / L>([&](auto W) MRDFT_INL {
+      constexpr int w = decltype(W)::value;
+      // accumulated gradient: upstream plus the parent's even bins (both
+      // children of a parent receive the same values)
+      static_for<0, L>([&](auto K) MRDFT_INL {
+        constexpr int k = decltype(K)::value;
+        constexpr int pk = (j == 4) ? k : ((w >> 1) * L + k);
+        G[w * L + k] = cadd(G[w * L + k], P[pk]);
+      });
+      static_for<0, h>([&](auto K) MRDFT_INL {
+        constexpr int k = decltype(K)::value;
+        Pn[w * h + k] = G[w * L + 2 * k];  // U^T
+      });
+      if constexpr (j == 1) {
+        acc[2 * w] = cadd(acc[2 * w], cadd(G[2 * w], G[2 * w + 1]));
+        acc[2 * w + 1] = cadd(acc[2 * w + 1], csub(G[2 * w], G[2 * w + 1]));
+      } else {
+        float2 zb[h];
+        static_for<0, h>([&](auto K) MRDFT_INL {
+          constexpr int k = decltype(K)::value;
+          zb[k] = G[w * L + 2 * k + 1];
+        });
+        idft_reg<h>(zb);
+        static_for<0, h>([&](auto N) MRDFT_INL {
+          constexpr int n = decltype(N)::value;
+          const float2 c = cmul_ct<L, (L - n) % L>(zb[n]);  // conj(w_L^n) zb[n]
+          acc[w * L + n] = cadd(acc[w * L + n], c);
+          acc[w * L + h + n] = csub(acc[w * L + h + n], c);
+        });
+      }
+    });
+#pragma unroll
+    for (int q = 0; q < 8; ++q) P[q] = Pn[q];
+  });
+}
+
+template <int TLOG, int NT>
+__global__ void __launch_bounds__(NT, 1) k_adj_tile(const AdjArgs a) {
+  constexpr int T = 1 << TLOG;
+  static_assert(T == 32 * NT, "tile = 32 samples per thread");
+  extern __shared__ __align__(1024) float2 sm[];
+  float2* ACC = sm;                        // T, x_bar accumulator (swz128)
+  float2* E[2] = {sm + T, sm + T + T / 2}; // even-bin propagation, level i in E[i & 1]
+  float2* Z = sm + 2 * T;                  // T/2, odd-bin inverse DFT work
+  AdjTileSig* TS = reinterpret_cast<AdjTileSig*>(sm + 2 * T + T / 2);
+  const int tid = threadIdx.x;
+  {
+    const int item = blockIdx.x;
+    if (item >= a.nitems) return;
+    const TileItem it = reinterpret_cast<const TileItem*>(a.items)[item];
+    const int tl = it.tlog;
+    const int Tn = it.nsig << tl;
+    const int tn_log = 31 - __clz(Tn);
+    if (tid < it.nsig) {
+      const SigDesc sd = a.sigs[a.sig_ids[it.sig_list + tid]];
+      const int64_t t0 = (int64_t)it.tile << tl;
+      TS[tid] = AdjTileSig{sd.in_off + t0, sd.out_off + t0, sd.m, 0};
+    }
+    // For a tile of a longer signal (one signal, m > tl) the large levels left
+    // contributions in acc and the level-(tl+1) even-bin propagation in e_in.
+    const SigDesc sd0 = a.sigs[a.sig_ids[it.sig_list]];
+    const bool below = sd0.m > tl;
+    __syncthreads();
+    for (int c = tid; c < (Tn >> 1); c += NT) {
+      const int e = c << 1;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (below) v = __ldcg(reinterpret_cast<const float4*>(a.acc + TS[0].x_base + e));
+      st4s_a(ACC + swz128(e), v);
+    }
+
+    // ---- levels tl .. 5 through shared memory
+    static_for<0, TLOG - 4>([&](auto II) MRDFT_INL {
+      constexpr int i = TLOG - decltype(II)::value;  // TLOG, ..., 5
+      constexpr int L = 1 << i, h = L / 2;
+      if (i <= tl) {
+        const float2* Ein = E[(i + 1) & 1];
+        float2* Eout = E[i & 1];
+        // G_i = g_i + P_i: even half -> Eout, conj(odd half) -> Z
+        for (int c = tid; c < (Tn >> 1); c += NT) {
+          const int e = c << 1;
+          const AdjTileSig& ts = TS[e >> tl];
+          const int off = e & ((1 << tl) - 1);
+          float4 g = __ldcs(reinterpret_cast<const float4*>(a.gy + ts.g_base + ((int64_t)(i - 1) << ts.m) + off));
+          const int w = e >> i, k = e & (L - 1);
+          float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (i == tl) {
+            if (below)
+              p = __ldcg(reinterpret_cast<const float4*>(a.e_in + sd0.aux_off + ((int64_t)(it.tile >> 1) << tl) + k));
+          } else {
+            const int pb = ((w >> 1) << i) + k;
+            const float2 pe = Ein[swzf(pb)], po = Ein[swzf(pb + 1)];
+            p = make_float4(pe.x, pe.y, po.x, po.y);
+          }
+          Eout[swzf(w * h + (k >> 1))] = make_float2(g.x + p.x, g.y + p.y);
+          Z[swzf(w * h + (k >> 1))] = make_float2(g.z + p.z, -(g.w + p.w));
+        }
+        __syncthreads();
+        auto src = [&](int b, int n) MRDFT_INL -> float2 { return Z[swzf(b * h + n)]; };
+        auto sink = [&](int b, int n, float2 v) MRDFT_INL {
+          const float2 c = cmulc(conjf2(v), tw_small(a.tw, i, n));  // conj(w^n) zb[n]
+          const int base = b << i;
+          const int i0 = swz128(base + n), i1 = swz128(base + h + n);
+          ACC[i0] = cadd(ACC[i0], c);
+          ACC[i1] = csub(ACC[i1], c);
+        };
+        fft_inplace<i - 1, NT, false>(Z, tn_log - i, a.tw, src, sink);
+        __syncthreads();
+      }
+    });
+
+    // ---- levels 4 .. 1 in registers, two 16-position chunks per thread
+#pragma unroll 1
+    for (int cc = 0; cc < 2; ++cc) {
+      const int chunk = 2 * tid + cc;
+      const int e = chunk << 4;
+      if (e >= Tn) continue;
+      float2 P[16], acc[16];
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        acc[q] = ACC[swz128(e + q)];
+        P[q] = E[1][swzf(((chunk >> 1) << 4) + q)];  // E_5 of the level-5 parent
+      }
+      const AdjTileSig& ts = TS[e >> tl];
+      const int off = e & ((1 << tl) - 1);
+      adj_chunk_levels_4_1(a, ts, off, P, acc);
+      float4* dst = reinterpret_cast<float4*>(a.gx + ts.x_base + off);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        __stcs(dst + q, make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y));
+    }
+  }
+}
+
+// ===================================================================== tiny
+
+// Signals with N <= 16: conjugate transpose of Eq. 1 term by term.
+__global__ void k_adj_tiny(const AdjArgs a) {
+  const SigDesc sd = a.sigs[a.sig_ids[blockIdx.x]];
+  const int N = 1 << sd.m;
+  const int n = threadIdx.x;
+  if (n >= N) return;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int i = 1; i <= sd.m; ++i) {
+    const int L = 1 << i, w = n >> i, nl = n & (L - 1);
+    for (int k = 0; k < L; ++k) {
+      const float2 g = a.gy[sd.out_off + ((int64_t)(i - 1) << sd.m) + (w << i) + k];
+      acc = cadd(acc, cmulc(g, tw_small(a.tw, i, (nl * k) & (L - 1))));
+    }
+  }
+  a.gx[sd.in_off + n] = acc;
+}
+
+// =================================================================== window
+
+// Accumulated gradient of a bin pair (2k, 2k+1) of window w at level i:
+// upstream g plus the parent's propagated even bins (none at the top level).
+__device__ __forceinline__ float4 adj_G(const AdjArgs& a, const SigDesc& sd, int i, int64_t w, int64_t k2) {
+  float4 g = __ldcs(reinterpret_cast<const float4*>(a.gy + sd.out_off + ((int64_t)(i - 1) << sd.m) + (w << i) + k2));
+  if (sd.m > i) {
+    const float4 p = __ldcg(reinterpret_cast<const float4*>(a.e_in + sd.aux_off + ((w >> 1) << i) + k2));
+    g.x += p.x; g.y += p.y; g.z += p.z; g.w += p.w;
+  }
+  return g;
+}
+
+__device__ __forceinline__ void acc_add(const AdjArgs& a, const SigDesc& sd, int i, int64_t idx, float2 c) {
+  float2* p = a.acc + sd.in_off + idx;
+  if (sd.m > i) {
+    float2 o = __ldcg(p);
+    c = cadd(o, c);
+  }
+  __stcg(p, c);
+}
+
+template <int LB>
+__device__ __forceinline__ void adj_window_level(const AdjArgs& a, const LevelItem& it, float2* Z) {
+  constexpr int NT = kWinThreads;
+  constexpr int h = 1 << LB;
+  const int i = LB + 1;
+  const SigDesc sd = a.sigs[it.sig];
+  const int64_t w = it.window;
+  for (int k = threadIdx.x; k < h; k += NT) {
+    const float4 g = adj_G(a, sd, i, w, 2 * (int64_t)k);
+    __stcg(a.e_out + sd.aux_off + (w << LB) + k, make_float2(g.x, g.y));
+    Z[swzf(k)] = make_float2(g.z, -g.w);
+  }
+  __syncthreads();
+  const int64_t ws = w << i;
+  auto src = [&](int, int n) -> float2 { return Z[swzf(n)]; };
+  auto sink = [&](int, int n, float2 v) MRDFT_INL {
+    const float2 c = cmulc(conjf2(v), tw_any(a.tw, i, n));
+    acc_add(a, sd, i, ws + n, c);
+    acc_add(a, sd, i, ws + h + n, make_float2(-c.x, -c.y));
+  };
+  fft_inplace<LB, NT, false>(Z, 0, a.tw, src, sink);
+}
+
+template <int LB>
+__global__ void __launch_bounds__(kWinThreads) k_adj_window(const AdjArgs a) {
+  extern __shared__ __align__(1024) float2 sm[];
+  if (blockIdx.x >= a.nitems) return;
+  adj_window_level<LB>(a, reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x], sm);
+}
+
+// =============================================================== two-pass
+
+// Adjoint of the forward two-pass level (h = Q * C, C = 2^12).
+// rows: item (sig, window, block) covers residues k2 in [k0, k0 + 4):
+//   G odd bins k = Q k1 + k2 -> IDFT_C over k1 -> times conj(w_h^(r k2))
+//   -> scratch U[window][k2][r]; even bins -> e_out.
+template <int QB>
+__device__ __forceinline__ void adj_rows_level(const AdjArgs& a, const LevelItem& it, float2* S) {
+  constexpr int NT = kPassThreads;
+  constexpr int CB = kColsLog, C = 1 << CB;
+  constexpr int KCB = 14 - CB, KC = 1 << KCB;
+  constexpr int HB = QB + CB;
+  const int i = HB + 1;
+  const SigDesc sd = a.sigs[it.sig];
+  const int64_t w = it.window;
+  const int k0 = it.block << KCB;
+  for (int e = threadIdx.x; e < KC * C; e += NT) {
+    const int j = e & (KC - 1), k1 = e >> KCB;
+    const int64_t k = ((int64_t)k1 << QB) + k0 + j;
+    const float4 g = adj_G(a, sd, i, w, 2 * k);
+    __stcg(a.e_out + sd.aux_off + (w << HB) + k, make_float2(g.x, g.y));
+    S[swzf((j << CB) + k1)] = make_float2(g.z, -g.w);
+  }
+  __syncthreads();
+  float2* U = a.scratch + sd.aux_off + (w << HB);
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((b << CB) + n)]; };
+  auto sink = [&](int b, int r, float2 v) MRDFT_INL {
+    const int k2 = k0 + b;
+    __stcg(U + ((int64_t)k2 << CB) + r, cmulc(conjf2(v), tw_any(a.tw, HB, (int64_t)r * k2)));
+  };
+  fft_inplace<CB, NT, false>(S, KCB, a.tw, src, sink);
+}
+
+template <int QB>
+__global__ void __launch_bounds__(kPassThreads) k_adj_rows(const AdjArgs a) {
+  extern __shared__ __align__(1024) float2 sm[];
+  if (blockIdx.x >= a.nitems) return;
+  adj_rows_level<QB>(a, reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x], sm);
+}
+
+// cols: item (sig, window, block) covers chunk offsets r in [r0, r0 + RC):
+//   U[window][k2][r] -> IDFT_Q over k2 -> zb[r + C q] -> conj(w_{2^i}^n) zb
+//   added to acc at n and subtracted at h + n.
+template <int QB>
+__device__ __forceinline__ void adj_cols_level(const AdjArgs& a, const LevelItem& it, float2* S) {
+  constexpr int NT = kPassThreads;
+  constexpr int CB = kColsLog, C = 1 << CB;
+  constexpr int Q = 1 << QB;
+  constexpr int RCB = 14 - QB, RC = 1 << RCB;
+  constexpr int HB = QB + CB;
+  constexpr int64_t h = (int64_t)1 << HB;
+  const int i = HB + 1;
+  const SigDesc sd = a.sigs[it.sig];
+  const int64_t w = it.window;
+  const int r0 = it.block << RCB;
+  const float2* U = a.scratch + sd.aux_off + (w << HB);
+  for (int e = threadIdx.x; e < RC * Q; e += NT) {
+    const int r = e & (RC - 1), k2 = e >> RCB;
+    S[swzf((r << QB) + k2)] = conjf2(__ldcg(U + ((int64_t)k2 << CB) + r0 + r));
+  }
+  __syncthreads();
+  const int64_t ws = w << i;
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((b << QB) + n)]; };
+  auto sink = [&](int b, int q, float2 v) MRDFT_INL {
+    const int64_t n = ((int64_t)q << CB) + r0 + b;
+    const float2 c = cmulc(conjf2(v), tw_any(a.tw, i, n));
+    acc_add(a, sd, i, ws + n, c);
+    acc_add(a, sd, i, ws + h + n, make_float2(-c.x, -c.y));
+  };
+  fft_inplace<QB, NT, true>(S, RCB, a.tw, src, sink);
+}
+
+template <int QB>
+__global__ void __launch_bounds__(kPassThreads) k_adj_cols(const AdjArgs a) {
+  extern __shared__ __align__(1024) float2 sm[];
+  if (blockIdx.x >= a.nitems) return;
+  adj_cols_level<QB>(a, reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x], sm);
+}
+
+// ================================================================ launchers
+
+static constexpr size_t kAdjTileSmem = (size_t)(2 * kTile + kTile / 2) * sizeof(float2) + kAdjMaxPack * sizeof(AdjTileSig);
+static constexpr size_t kAdjWinSmem = (size_t)(1 << kWinMaxLog) * sizeof(float2);
+static constexpr size_t kAdjPassSmem = (size_t)kPassElems * sizeof(float2);
+
+using AdjKernel = void (*)(const AdjArgs);
+static AdjKernel adj_win_kernel(int level) {
+  switch (level) {
+    case 13: return k_adj_window<12>;
+    case 14: return k_adj_window<13>;
+    default: return nullptr;
+  }
+}
+template <int QB>
+static void adj_pass_pair(int level, AdjKernel* r, AdjKernel* c) {
+  if constexpr (QB <= 13) {
+    if (level == QB + kColsLog + 1) {
+      *r = k_adj_rows<QB>;
+      *c = k_adj_cols<QB>;
+      return;
+    }
+    adj_pass_pair<QB + 1>(level, r, c);
+  }
+}
+
+cudaError_t set_adj_attributes() {
+  cudaError_t e = cudaFuncSetAttribute(k_adj_tile<kTileLog, kTileThreads>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjTileSmem);
+  for (int lv = 13; lv <= 14 && e == cudaSuccess; ++lv)
+    e = cudaFuncSetAttribute(adj_win_kernel(lv), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
+  for (int lv = 15; lv <= 26 && e == cudaSuccess; ++lv) {
+    AdjKernel r = nullptr, c = nullptr;
+    adj_pass_pair<2>(lv, &r, &c);
+    e = cudaFuncSetAttribute(r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjPassSmem);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjPassSmem);
+  }
+  return e;
+}
+
+cudaError_t launch_adj_tile(const AdjArgs& a, int grid, cudaStream_t s) {
+  k_adj_tile<kTileLog, kTileThreads><<<grid, kTileThreads, kAdjTileSmem, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_adj_tiny(const AdjArgs& a, int nsig_tiny, cudaStream_t s) {
+  k_adj_tiny<<<nsig_tiny, 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s) {
+  AdjKernel k = adj_win_kernel(a.level);
+  if (!k) return cudaErrorInvalidValue;
+  k<<<grid, kWinThreads, kAdjWinSmem, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s) {
+  AdjKernel r = nullptr, c = nullptr;
+  adj_pass_pair<2>(a.level, &r, &c);
+  if (!r) return cudaErrorInvalidValue;
+  r<<<grid, kPassThreads, kAdjPassSmem, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_adj_cols(const AdjArgs& a, int grid, cudaStream_t s) {
+  AdjKernel r = nullptr, c = nullptr;
+  adj_pass_pair<2>(a.level, &r, &c);
+  if (!c) return cudaErrorInvalidValue;
+  c<<<grid, kPassThreads, kAdjPassSmem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace mrdft

@@ -1,0 +1,170 @@
+// Device-side building blocks of the MrDFT library (sm_103a).
+//
+// Complex values are float2 (re, im), FP32, interleaved -- the complex64
+// layout of the C ABI.  Forward transforms use the sign exp(-j 2 pi n k / L)
+// of the DEF matrix E_{2^i} (Sec. 2 of Andreatto & Cariow); nothing is
+// normalised.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+// Forces inlining of the small lambdas (static_for bodies, FFT sources and
+// sinks) so the register arrays they touch never go to local memory.
+#define MRDFT_INL __attribute__((always_inline))
+
+namespace mrdft {
+
+// ------------------------------------------------------------ complex math
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// a * conj(b)
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.y, b.x, -a.x * b.y));
+}
+// a * (-j)
+__device__ __forceinline__ float2 cmul_mj(float2 a) { return make_float2(a.y, -a.x); }
+// a * (+j)
+__device__ __forceinline__ float2 cmul_pj(float2 a) { return make_float2(-a.y, a.x); }
+
+// ------------------------------------------------- compile-time twiddles
+// cos(2 pi q / 64) for q = 0..16 as FP64 literals; every compile-time twiddle
+// below is one of these (or its negation), rounded once to FP32.
+__host__ __device__ constexpr double kcos64(int q) {
+  return q == 0 ? 1.0 : q == 1 ? 0.99518472667219688624 : q == 2 ? 0.98078528040323044913
+       : q == 3 ? 0.95694033573220886494 : q == 4 ? 0.92387953251128675613
+       : q == 5 ? 0.88192126434835502971 : q == 6 ? 0.83146961230254523708
+       : q == 7 ? 0.77301045336273696081 : q == 8 ? 0.70710678118654752440
+       : q == 9 ? 0.63439328416364549822 : q == 10 ? 0.55557023301960222474
+       : q == 11 ? 0.47139673682599764856 : q == 12 ? 0.38268343236508977173
+       : q == 13 ? 0.29028467725446236764 : q == 14 ? 0.19509032201612826785
+       : q == 15 ? 0.09801714032956060199 : 0.0;
+}
+
+// w_L^E = exp(-j 2 pi E / L) for L | 64, as compile-time constants.
+template <int L, int E>
+struct CTw {
+  static constexpr int q = (E * (64 / L)) & 63;
+  static constexpr int quad = q >> 4, r = q & 15;
+  static constexpr double c = kcos64(r), s = kcos64(16 - r);
+  static constexpr float re = (float)(quad == 0 ? c : quad == 1 ? -s : quad == 2 ? -c : s);
+  static constexpr float im = (float)(quad == 0 ? -s : quad == 1 ? -c : quad == 2 ? s : c);
+};
+
+// a * w_L^E with the trivial twiddles (1, -j, -1, +j) reduced to swaps/negations
+template <int L, int E>
+__device__ __forceinline__ float2 cmul_ct(float2 a) {
+  constexpr int q = CTw<L, E>::q;
+  if constexpr (q == 0) return a;
+  else if constexpr (q == 16) return cmul_mj(a);
+  else if constexpr (q == 32) return make_float2(-a.x, -a.y);
+  else if constexpr (q == 48) return cmul_pj(a);
+  else return cmul(a, make_float2(CTw<L, E>::re, CTw<L, E>::im));
+}
+
+template <int V>
+struct IC { static constexpr int value = V; };
+
+template <int B, int E, int S = 1, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(IC<B>{});
+    static_for<B + S, E, S>(f);
+  }
+}
+
+__host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
+__host__ __device__ constexpr int bitrevc(int v, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r |= ((v >> b) & 1) << (bits - 1 - b);
+  return r;
+}
+
+template <int R, int LEN>
+__device__ __forceinline__ void dif_stage(float2 (&v)[R]) {
+  constexpr int half = LEN / 2;
+  static_for<0, R, LEN>([&](auto S) MRDFT_INL {
+    static_for<0, half>([&](auto J) MRDFT_INL {
+      constexpr int s = decltype(S)::value, j = decltype(J)::value;
+      float2 a = v[s + j], b = v[s + j + half];
+      v[s + j] = cadd(a, b);
+      v[s + j + half] = cmul_ct<LEN, j>(csub(a, b));
+    });
+  });
+  if constexpr (LEN > 2) dif_stage<R, LEN / 2>(v);
+}
+
+// In-register DFT of length R (power of two, 1 <= R <= 64), natural order in
+// and out: radix-2 decimation in frequency with compile-time twiddles, then a
+// compile-time bit reversal (register renaming only).
+template <int R>
+__device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
+  if constexpr (R >= 2) {
+    dif_stage<R, R>(v);
+    float2 t[R];
+    static_for<0, R>([&](auto K) MRDFT_INL {
+      constexpr int k = decltype(K)::value;
+      t[k] = v[bitrevc(k, ilog2c(R))];
+    });
+    static_for<0, R>([&](auto K) MRDFT_INL { v[decltype(K)::value] = t[decltype(K)::value]; });
+  }
+}
+
+// Unnormalised inverse (sign +j): conj(DFT(conj(v))).
+template <int R>
+__device__ __forceinline__ void idft_reg(float2 (&v)[R]) {
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k].y = -v[k].y;
+  dft_reg<R>(v);
+#pragma unroll
+  for (int k = 0; k < R; ++k) v[k].y = -v[k].y;
+}
+
+// ------------------------------------------------------ shared-memory maps
+// Level / input tile buffers: rows of 16 complex (128 B); the 16-B chunk c of
+// row r lives at chunk c ^ (r & 7) -- the 128-byte swizzle a TMA tensor copy
+// with CU_TENSOR_MAP_SWIZZLE_128B produces.  Index in float2 units.
+__device__ __forceinline__ int swz128(int e) {
+  int r = e >> 4;
+  return (r << 4) | ((((e >> 1) & 7) ^ (r & 7)) << 1) | (e & 1);
+}
+// FFT work buffers: XOR the low 4 index bits with bits 4..7 and 8..11 so that
+// power-of-two strides up to 2^12 spread over all banks (8-byte elements).
+__device__ __forceinline__ int swzf(int e) { return e ^ (((e >> 4) ^ (e >> 8)) & 15); }
+
+// ------------------------------------------------------------ twiddle tables
+// Device tables written once by the plan from FP64 host values rounded once:
+//   tw13[e] = w_{2^13}^e, e < 2^13   (every FFT of length <= 2^13 and the
+//                                       level twiddles w_{2^i}^n, i <= 13)
+//   twlo[e] = w_{2^28}^e, e < 2^14 and twhi[e] = w_{2^28}^{e * 2^14},
+//   e < 2^14: w_{2^28}^e = twhi[e >> 14] * twlo[e & 16383] for larger levels
+//   (the product of two once-rounded values: one extra FP32 rounding).
+struct Twiddles {
+  const float2* tw13;
+  const float2* twlo;
+  const float2* twhi;
+};
+constexpr int kTwLog = 13;
+constexpr int kTwBigLog = 28;
+constexpr int kTwSplit = 14;
+
+// w_{2^l}^e, l <= 13
+__device__ __forceinline__ float2 tw_small(const Twiddles& T, int l, int e) {
+  return __ldg(&T.tw13[(e << (kTwLog - l)) & ((1 << kTwLog) - 1)]);
+}
+// w_{2^l}^e for l <= 28: one table entry for l <= 13, else a product of two
+__device__ __forceinline__ float2 tw_any(const Twiddles& T, int l, int64_t e) {
+  if (l <= kTwLog) return tw_small(T, l, (int)(e & ((1 << l) - 1)));
+  uint32_t q = (uint32_t)((e << (kTwBigLog - l)) & ((1 << kTwBigLog) - 1));
+  return cmul(__ldg(&T.twhi[q >> kTwSplit]), __ldg(&T.twlo[q & ((1 << kTwSplit) - 1)]));
+}
+
+// ------------------------------------------------------------ status word
+enum : int { kStatusOk = 0, kStatusTimeout = 5, kStatusBadItem = 6 };
+__device__ __forceinline__ void set_status(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+}  // namespace mrdft

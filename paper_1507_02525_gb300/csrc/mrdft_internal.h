@@ -1,0 +1,95 @@
+// Host/device shared descriptors of the MrDFT library (not part of the C ABI).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "mrdft_common.cuh"
+
+namespace mrdft {
+
+// One signal of a plan.  Offsets count complex samples (complex64 input) or
+// real samples (FP32 input) for x, complex values for y; N = 2^m.
+struct SigDesc {
+  int64_t in_off;   // first sample of the signal in x
+  int64_t out_off;  // first output of level 1 in y; level i at out_off + (i-1) N
+  int64_t aux_off;  // first element of the signal in the per-signal scratch
+  int32_t m;        // log2 N
+  int32_t pad;
+};
+
+// In-tile work item: levels 1..tlog of `nsig` signals listed at
+// sig_ids[sig_list ..] (each of length 2^tlog when nsig > 1), or of the
+// samples [tile * 2^tlog, (tile + 1) * 2^tlog) of one longer signal.
+struct TileItem {
+  int32_t sig_list;
+  int16_t nsig;
+  int16_t tlog;
+  int32_t tile;
+  int32_t pad;
+};
+
+// Large-level work item: signal, window at level `level`, and a block index
+// inside the window (column block or bin block for the two-pass levels).
+struct LevelItem {
+  int32_t sig;
+  int32_t window;
+  int32_t block;
+  int32_t pad;
+};
+
+constexpr int kTileLog = 12;                 // in-tile levels 1..12
+constexpr int kTile = 1 << kTileLog;         // 4096 samples per tile
+constexpr int kTileThreads = 128;            // 32 samples per thread
+constexpr int kWinMaxLog = 13;               // one CTA FFT holds up to 2^13 points
+constexpr int kWinThreads = 256;
+constexpr int kColsLog = 12;                 // two-pass levels: FFT_C over 2^12 ...
+constexpr int kPassElems = 1 << 14;          // ... and 2^14 points of smem per CTA
+constexpr int kPassThreads = 256;
+
+struct FwdArgs {
+  const void* x;  // float2* (complex64) or float* (real FP32)
+  int in_real;
+  float2* y;
+  const SigDesc* sigs;
+  const int32_t* sig_ids;
+  const void* items;  // TileItem* or LevelItem*
+  int nitems;
+  int level;          // large-level kernels: level i being built
+  float2* scratch;    // two-pass levels: intermediate, N/2 per signal
+  Twiddles tw;
+  int* status;
+};
+
+struct AdjArgs {
+  const float2* gy;   // upstream gradient, same layout as y
+  float2* gx;         // complex64 gradient of x
+  const SigDesc* sigs;
+  const int32_t* sig_ids;
+  const void* items;
+  int nitems;
+  int level;
+  const float2* e_in;  // even-bin propagation from level+1 (N/2 per signal)
+  float2* e_out;       // even-bin propagation to level-1 (N/2 per signal)
+  float2* acc;         // x_bar contributions of the large levels (N per signal)
+  float2* scratch;     // two-pass levels intermediate (N/2 per signal)
+  int first;           // 1 when this is the top level (no e_in, acc written not added)
+  Twiddles tw;
+  int* status;
+};
+
+// launchers (defined in the .cu files)
+cudaError_t launch_fwd_tile(const FwdArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_fwd_tiny(const FwdArgs& a, int nsig_tiny, cudaStream_t s);
+cudaError_t launch_fwd_window(const FwdArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_fwd_rows(const FwdArgs& a, int grid, cudaStream_t s);
+
+cudaError_t launch_adj_tile(const AdjArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_adj_tiny(const AdjArgs& a, int nsig_tiny, cudaStream_t s);
+cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_adj_cols(const AdjArgs& a, int grid, cudaStream_t s);
+
+cudaError_t set_kernel_attributes();
+
+}  // namespace mrdft

@@ -1,0 +1,359 @@
+"""GPU parity of the CUDA MrDFT against the FP64 oracle, through the C ABI.
+
+Every input comes from the seeded generators in paper_1507_02525_gb300.inputs;
+every expected value from oracle/.  Sizes run from N = 2 (the degenerate
+level-1-only case) through the tile (2^12), window (2^13, 2^14) and two-pass
+(2^15 ..) regimes to the full 2^24 signal and the 2^26 maximum.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from paper_1507_02525_gb300 import _lib, api, inputs  # noqa: E402
+
+from tests._parity import check_adjoint, check_forward_levels  # noqa: E402
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    torch.cuda.set_device(0)
+    yield
+    torch.cuda.synchronize()
+
+
+def run_forward(plan, x_np):
+    """Forward through the C ABI with torch-allocated device buffers."""
+    xt = torch.from_numpy(np.ascontiguousarray(x_np)).cuda()
+    y = torch.empty(plan.out_elems, dtype=torch.complex64, device="cuda")
+    plan.forward(xt.data_ptr(), y.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    plan.status_poll()
+    return y.cpu().numpy()
+
+
+def run_adjoint(plan, gy_np):
+    gyt = torch.from_numpy(np.ascontiguousarray(gy_np)).cuda()
+    gx = torch.empty(plan.in_elems, dtype=torch.complex64, device="cuda")
+    plan.adjoint(gyt.data_ptr(), gx.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    plan.status_poll()
+    return gx.cpu().numpy()
+
+
+def split_out(y, lengths):
+    out, o = [], 0
+    for n in lengths:
+        m = int(n).bit_length() - 1
+        out.append(y[o:o + m * n].reshape(m, n))
+        o += m * n
+    return out
+
+
+def split_in(x, lengths):
+    out, o = [], 0
+    for n in lengths:
+        out.append(x[o:o + n])
+        o += n
+    return out
+
+
+# ------------------------------------------------------------------ forward
+
+@pytest.mark.parametrize("m", list(range(1, 21)))
+def test_forward_single(oracle, m):
+    N = 1 << m
+    x = inputs.complex_signals(1, N, seed=1000 + m)[0]
+    plan = _lib.Plan([N], 1)
+    y = run_forward(plan, x).reshape(m, N)
+    ref = oracle.forward(x.astype(np.complex128))
+    check_forward_levels(y, ref, x, f"N=2^{m}")
+
+
+@pytest.mark.parametrize("m", [5, 8, 12, 13, 15])
+def test_forward_real_input(oracle, m):
+    N = 1 << m
+    x = inputs.real_signals(3, N, seed=50 + m)
+    plan = _lib.Plan([N], 3, real_input=True)
+    y = run_forward(plan, x.reshape(-1)).reshape(3, m, N)
+    for s in range(3):
+        ref = oracle.forward(x[s].astype(np.complex128))
+        check_forward_levels(y[s], ref, x[s], f"real N=2^{m} s={s}")
+
+
+@pytest.mark.parametrize("B,m", [(8, 10), (3, 16), (256, 6), (5, 5), (130, 7), (2, 14)])
+def test_forward_uniform_batch(oracle, B, m):
+    N = 1 << m
+    x = inputs.complex_signals(B, N, seed=7 * B + m)
+    plan = _lib.Plan([N], B)
+    y = run_forward(plan, x.reshape(-1)).reshape(B, m, N)
+    for s in sorted(set([0, B - 1, B // 2])):
+        ref = oracle.forward(x[s].astype(np.complex128))
+        check_forward_levels(y[s], ref, x[s], f"B={B} N=2^{m} s={s}")
+
+
+@pytest.mark.parametrize("real", [False, True])
+def test_forward_ragged(oracle, real):
+    rng = np.random.default_rng(77)
+    ks = list(rng.integers(1, 18, size=40)) + [1, 2, 3, 4, 12, 13, 14, 15, 17]
+    rng.shuffle(ks)
+    lengths = [1 << int(k) for k in ks]
+    total = sum(lengths)
+    x = (inputs.real_signals(1, total, seed=78)[0] if real
+         else inputs.complex_signals(1, total, seed=78)[0])
+    plan = _lib.Plan(lengths, len(lengths), real_input=real)
+    assert plan.out_elems == sum((n.bit_length() - 1) * n for n in lengths)
+    ys = split_out(run_forward(plan, x), lengths)
+    for s, (xs, ys_) in enumerate(zip(split_in(x, lengths), ys)):
+        ref = oracle.forward(xs.astype(np.complex128))
+        check_forward_levels(ys_, ref, xs, f"ragged s={s} N={len(xs)}")
+
+
+def test_forward_graph_replay(oracle):
+    N, B = 1 << 15, 2
+    x = inputs.complex_signals(B, N, seed=5)
+    plan = _lib.Plan([N], B, graph=True)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty(plan.out_elems, dtype=torch.complex64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            plan.forward(xt.data_ptr(), y.data_ptr(), s.cuda_stream)
+    s.synchronize()
+    y1 = y.cpu().numpy().reshape(B, 15, N)
+    plan2 = _lib.Plan([N], B)
+    y2 = run_forward(plan2, x.reshape(-1)).reshape(B, 15, N)
+    np.testing.assert_array_equal(y1, y2)  # graph replay = direct launch, bit for bit
+    ref = oracle.forward(x[1].astype(np.complex128))
+    check_forward_levels(y1[1], ref, x[1], "graph")
+
+
+def test_forward_deterministic():
+    N = 1 << 17
+    x = inputs.complex_signals(1, N, seed=9)[0]
+    plan = _lib.Plan([N], 1)
+    np.testing.assert_array_equal(run_forward(plan, x), run_forward(plan, x))
+
+
+def test_forward_host_entry(oracle):
+    N, B = 1 << 13, 3
+    x = inputs.complex_signals(B, N, seed=21)
+    plan = _lib.Plan([N], B)
+    y_host = np.empty(plan.out_elems, dtype=np.complex64)
+    plan.forward_host(x.ctypes.data, y_host.ctypes.data, 0)
+    np.testing.assert_array_equal(y_host, run_forward(plan, x.reshape(-1)))
+
+
+def test_forward_api_shapes(oracle):
+    x = inputs.complex_signals(2, 256, seed=3)
+    y = api.mrdft(torch.from_numpy(x).cuda())
+    assert y.shape == (2, 8, 256) and y.dtype == torch.complex64
+    y1 = api.mrdft(torch.from_numpy(x[0]).cuda())
+    assert y1.shape == (8, 256)
+    np.testing.assert_array_equal(y1.cpu().numpy(), y[0].cpu().numpy())
+
+
+def test_closed_forms_on_gpu():
+    """Impulse at a window start -> all-ones spectra; constant -> DC only."""
+    N, m = 1 << 14, 14
+    x = np.zeros(N, np.complex64)
+    x[0] = 1.0
+    y = run_forward(_lib.Plan([N], 1), x).reshape(m, N)
+    for i in range(1, m + 1):
+        L = 1 << i
+        np.testing.assert_allclose(y[i - 1][:L], 1.0, atol=1e-6)
+        np.testing.assert_allclose(y[i - 1][L:], 0.0, atol=1e-6)
+    c = np.full(N, 0.5 - 0.25j, np.complex64)
+    y = run_forward(_lib.Plan([N], 1), c).reshape(m, N)
+    for i in range(1, m + 1):
+        L = 1 << i
+        blk = y[i - 1].reshape(-1, L)
+        np.testing.assert_allclose(blk[:, 0], (0.5 - 0.25j) * L, rtol=1e-6)
+        assert np.abs(blk[:, 1:]).max() <= 1e-6 * L
+
+
+# -------------------------------------------------------- full-size workloads
+
+@pytest.fixture(scope="module")
+def big_signal():
+    x = inputs.complex_signals(1, 1 << 24, seed=1)[0]
+    plan = _lib.Plan([1 << 24], 1)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty(plan.out_elems, dtype=torch.complex64, device="cuda")
+    plan.forward(xt.data_ptr(), y.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    plan.status_poll()
+    return x, y.view(24, 1 << 24)
+
+
+def test_single_16m_every_level(oracle, big_signal):
+    """N = 2^24: every level compared in full with the oracle's FFT path."""
+    x, y = big_signal
+    x128 = x.astype(np.complex128)
+    xn = float(np.linalg.norm(x128))
+    for i in range(1, 25):
+        ref = oracle.forward_level(x128, i)
+        d = y[i - 1].cpu().numpy().astype(np.complex128) - ref
+        rel = np.linalg.norm(d) / np.linalg.norm(ref)
+        assert rel <= 2e-6 * i, f"level {i}: rel {rel:.3e}"
+        assert np.abs(d).max() <= 1e-5 * xn, f"level {i}: max abs"
+
+
+def test_single_16m_sampled_bins(oracle, big_signal):
+    """Independent check: bins evaluated one by one with the direct sum of Eq. 1."""
+    x, y = big_signal
+    x128 = x.astype(np.complex128)
+    xn = float(np.linalg.norm(x128))
+    rng = np.random.default_rng(123)
+    for i in (1, 2, 7, 12, 13, 15, 18, 20, 24):
+        for pos in list(rng.integers(0, 1 << 24, size=3)) + [0, (1 << 24) - 1]:
+            ref = oracle.bin_value(x128, i, int(pos))
+            got = complex(y[i - 1, int(pos)].item())
+            assert abs(got - ref) <= 1e-5 * xn, f"level {i} pos {pos}"
+
+
+def test_batch_256x64k(oracle):
+    B, N, m = 256, 1 << 16, 16
+    x = inputs.complex_signals(B, N, seed=2)
+    y = run_forward(_lib.Plan([N], B), x.reshape(-1)).reshape(B, m, N)
+    for s in (0, 1, 100, 254, 255):
+        ref = oracle.forward(x[s].astype(np.complex128))
+        check_forward_levels(y[s], ref, x[s], f"batch s={s}")
+
+
+def test_ragged_1024(oracle):
+    lengths, samples = inputs.ragged_real()
+    lengths = [int(v) for v in lengths]
+    plan = _lib.Plan(lengths, len(lengths), real_input=True)
+    ys = split_out(run_forward(plan, samples), lengths)
+    xs = split_in(samples, lengths)
+    rng = np.random.default_rng(4)
+    pick = set(rng.integers(0, len(lengths), size=24).tolist())
+    pick |= {int(np.argmax(lengths)), int(np.argmin(lengths)), 0, len(lengths) - 1}
+    for s in sorted(pick):
+        ref = oracle.forward(xs[s].astype(np.complex128))
+        check_forward_levels(ys[s], ref, xs[s], f"ragged1024 s={s}")
+
+
+def test_maximum_length_2_26(oracle):
+    """The largest length a plan accepts, checked on sampled bins."""
+    N = 1 << 26
+    x = inputs.complex_signals(1, N, seed=26)[0]
+    plan = _lib.Plan([N], 1)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty(plan.out_elems, dtype=torch.complex64, device="cuda")
+    plan.forward(xt.data_ptr(), y.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    plan.status_poll()
+    y = y.view(26, N)
+    x128 = x.astype(np.complex128)
+    xn = float(np.linalg.norm(x128))
+    for i, pos in [(1, 5), (5, N - 1), (12, 123456), (16, 7_000_001), (21, 3), (26, 0), (26, N // 2 + 1)]:
+        ref = oracle.bin_value(x128, i, pos)
+        assert abs(complex(y[i - 1, pos].item()) - ref) <= 1e-5 * xn, f"level {i} pos {pos}"
+    del y, xt
+    torch.cuda.empty_cache()
+
+
+# ------------------------------------------------------------------ adjoint
+
+@pytest.mark.parametrize("m", list(range(1, 19)))
+def test_adjoint_single(oracle, m):
+    N = 1 << m
+    g = inputs.targets(1, N, seed=300 + m)[0]
+    gx = run_adjoint(_lib.Plan([N], 1), g.reshape(-1))
+    ref = oracle.adjoint(g.astype(np.complex128))
+    check_adjoint(gx, ref, g, f"N=2^{m}")
+
+
+def test_adjoint_ragged(oracle):
+    rng = np.random.default_rng(88)
+    ks = list(rng.integers(1, 17, size=30)) + [1, 4, 5, 12, 13, 14, 15, 16]
+    rng.shuffle(ks)
+    lengths = [1 << int(k) for k in ks]
+    plan = _lib.Plan(lengths, len(lengths))
+    gy = inputs.complex_signals(1, plan.out_elems, seed=89)[0]
+    gx = split_in(run_adjoint(plan, gy), lengths)
+    gys = split_out(gy, lengths)
+    for s in range(len(lengths)):
+        ref = oracle.adjoint(gys[s].astype(np.complex128))
+        check_adjoint(gx[s], ref, gys[s], f"ragged s={s}")
+
+
+def test_adjoint_dot_product():
+    """<M x, g> = <x, M^H g> with both sides on the GPU (N = 2^18, batch 4)."""
+    B, N = 4, 1 << 18
+    x = inputs.complex_signals(B, N, seed=11)
+    g = inputs.targets(B, N, seed=12)
+    plan = _lib.Plan([N], B)
+    y = run_forward(plan, x.reshape(-1)).astype(np.complex128)
+    gx = run_adjoint(plan, g.reshape(-1)).astype(np.complex128)
+    lhs = np.vdot(g.reshape(-1).astype(np.complex128), y)
+    rhs = np.vdot(gx, x.reshape(-1).astype(np.complex128))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_adjoint_grad_workload(oracle):
+    """64 x 2^18 loss sum_i 2^-i ||Y_i - T_i||^2: gradient through autograd
+    against the oracle's adjoint of the oracle's residual (sampled signals)."""
+    B, N, m = 64, 1 << 18, 18
+    x = inputs.complex_signals(B, N, seed=4)
+    T = inputs.targets(B, N, seed=5)
+    w = torch.tensor([2.0 ** -(i + 1) for i in range(m)], device="cuda").view(1, m, 1)
+    xt = torch.from_numpy(x).cuda().requires_grad_(True)
+    Tt = torch.from_numpy(T).cuda()
+    Y = api.MrDFT.apply(xt)
+    loss = (w * (Y - Tt).abs() ** 2).sum()
+    loss.backward()
+    g = xt.grad.cpu().numpy()
+    wn = 2.0 ** -np.arange(1, m + 1)
+    for s in (0, 31, 63):
+        Yr = oracle.forward(x[s].astype(np.complex128))
+        gy = 2 * wn[:, None] * (Yr - T[s].astype(np.complex128))
+        ref = oracle.adjoint(gy)
+        rel = np.linalg.norm(g[s] - ref) / np.linalg.norm(ref)
+        assert rel <= 1e-5, f"signal {s}: grad rel {rel:.3e}"
+
+
+def test_autograd_finite_differences(oracle):
+    """N = 2^8 slice: autograd gradient vs central differences of the FP64 oracle loss."""
+    N, m = 256, 8
+    x = inputs.complex_signals(1, N, seed=40)[0]
+    T = inputs.targets(1, N, seed=41)[0].astype(np.complex128)
+    wn = 2.0 ** -np.arange(1, m + 1)
+    xt = torch.from_numpy(x).cuda().requires_grad_(True)
+    Y = api.MrDFT.apply(xt)
+    loss = (torch.from_numpy(wn).cuda().float().view(m, 1)
+            * (Y - torch.from_numpy(T.astype(np.complex64)).cuda()).abs() ** 2).sum()
+    loss.backward()
+    g = xt.grad.cpu().numpy().astype(np.complex128)
+    x128 = x.astype(np.complex128)
+
+    def L(v):
+        return float((wn[:, None] * np.abs(oracle.forward(v) - T) ** 2).sum())
+
+    eps = 1e-6
+    rng = np.random.default_rng(0)
+    for p in rng.choice(N, size=24, replace=False):
+        for unit in (1.0, 1j):
+            e = np.zeros(N, complex)
+            e[p] = unit * eps
+            fd = (L(x128 + e) - L(x128 - e)) / (2 * eps)
+            an = g[p].real if unit == 1.0 else g[p].imag
+            assert abs(fd - an) <= 1e-4 * max(1.0, abs(fd)), f"p={p} unit={unit}: fd {fd} vs {an}"
+
+
+def test_autograd_real_input(oracle):
+    N, m = 1 << 12, 12
+    x = inputs.real_signals(2, N, seed=70)
+    xt = torch.from_numpy(x).cuda().requires_grad_(True)
+    Y = api.MrDFT.apply(xt)
+    (Y.abs() ** 2).sum().backward()
+    g = xt.grad.cpu().numpy()
+    for s in range(2):
+        Yr = oracle.forward(x[s].astype(np.complex128))
+        ref = oracle.adjoint(2 * Yr).real
+        np.testing.assert_allclose(g[s], ref, rtol=0, atol=1e-5 * np.abs(ref).max())
