@@ -1,0 +1,432 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 MrDFT: input Gsamples/s and fraction of the HBM roofline.
+
+Default workload (one GPU): one complex64 signal of N = 2^24 samples, i.i.d.
+N(0,1) (seed 1), all 24 levels.  A step is one forward MrDFT of that signal;
+the adjoint of the same size is timed the same way and reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload single_16m|batch_256x64k|ragged_1024|grad_64x256k|single_1k]
+
+Under torchrun each rank runs its own replica of the workload on its own GPU
+(the transform has no cross-signal exchange): weak scaling, barrier-bracketed
+CUDA-event timing, max over ranks.  `--impl reference` times the FP64 CPU
+oracle (the only reference this paper has) on a bounded sample of the same
+workload on the host cores.  One JSON line is printed by rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MrDFT input Gsamples/s & % of HBM roofline (fwd, adjoint) on 1 GB300"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def log2i(n: int) -> int:
+    return int(n).bit_length() - 1
+
+
+# ------------------------------------------------------------------ workloads
+
+def workload_spec(name: str):
+    """(lengths list, real_input, description) of a named workload."""
+    from paper_1507_02525_gb300 import inputs
+    if name == "single_16m":
+        return [1 << 24], False, "1 complex64 signal, N=2^24, re/im i.i.d. N(0,1) seed 1, all 24 levels"
+    if name == "single_1k":
+        return [1 << 10], False, "1 complex64 signal, N=2^10, seed 0"
+    if name == "single_4m":
+        return [1 << 22], False, "1 complex64 signal, N=2^22, seed 1 (profiling size)"
+    if name == "tiles_4096x4k":
+        return [1 << 12] * 4096, False, "4096 complex64 signals of N=2^12, seed 6 (in-tile levels only)"
+    if name == "batch_256x64k":
+        return [1 << 16] * 256, False, "256 complex64 signals of N=2^16, seed 2, one launch set"
+    if name == "grad_64x256k":
+        return [1 << 18] * 64, False, "64 complex64 signals of N=2^18, seed 4"
+    if name == "ragged_1024":
+        lengths, _ = inputs.ragged_real()
+        return [int(v) for v in lengths], True, "1024 real FP32 signals, N=2^k, k~U{8..18} seed 3"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def make_input(name: str):
+    from paper_1507_02525_gb300 import inputs
+    if name == "single_16m":
+        return inputs.complex_signals(1, 1 << 24, seed=1).reshape(-1)
+    if name == "single_1k":
+        return inputs.complex_signals(1, 1 << 10, seed=0).reshape(-1)
+    if name == "single_4m":
+        return inputs.complex_signals(1, 1 << 22, seed=1).reshape(-1)
+    if name == "tiles_4096x4k":
+        return inputs.complex_signals(4096, 1 << 12, seed=6).reshape(-1)
+    if name == "batch_256x64k":
+        return inputs.complex_signals(256, 1 << 16, seed=2).reshape(-1)
+    if name == "grad_64x256k":
+        return inputs.complex_signals(64, 1 << 18, seed=4).reshape(-1)
+    if name == "ragged_1024":
+        return inputs.ragged_real()[1]
+    raise SystemExit(name)
+
+
+def algorithmic_bytes(lengths, real_input: bool) -> int:
+    """Roofline bytes of one forward (or adjoint): x once + every level once."""
+    in_b = 4 if real_input else 8
+    return sum(n * in_b + 8 * log2i(n) * n for n in lengths)
+
+
+# ----------------------------------------------------------------- utilities
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, copy read+write)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback (6.8 TB/s, no MEASURED_PEAKS.json)"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1507_02525_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` from profiles/ncu_traffic.txt, only if the
+    recorded source hash matches the kernels built now (else None)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    cur = kernel_source_hash()
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 4 and not line.startswith("#"):
+            h, k, w, b = parts[:4]
+            if h == cur and k == kernel and w == workload:
+                return int(float(b))
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", self.gpu_id],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [v.strip() for v in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_max": max(power) if power else None, "reasons": sorted(reasons)}
+
+
+# ------------------------------------------------------------- oracle timing
+
+def oracle_sample(lengths, x_np, budget_s: float = 15.0):
+    """Time the FP64 oracle (per-window FFT path) on a bounded sample and
+    extrapolate to the whole workload.
+
+    For each signal length present, level i is timed on a window-aligned slice
+    of max(2^i, 2^20) samples (the oracle's per-level cost is proportional to
+    the samples covered) and scaled to the full signal; levels are visited in
+    order until the time budget is spent, later levels are extrapolated as
+    proportional to i.  Returns (samples/s, cores, description)."""
+    import numpy as np
+    from oracle import oracle as O
+    O.build()
+    cores = O.num_threads()
+    total_est = 0.0
+    timed_levels = 0
+    spent = 0.0
+    uniq = {}
+    off = 0
+    for n in lengths:
+        uniq.setdefault(n, (off, 0))
+        uniq[n] = (uniq[n][0], uniq[n][1] + 1)
+        off += n
+    for n, (first, count) in sorted(uniq.items()):
+        m = log2i(n)
+        x = np.asarray(x_np[first:first + n], dtype=np.complex128)
+        last = None
+        for i in range(1, m + 1):
+            if spent < budget_s:
+                s = max(1 << i, min(n, 1 << 20))
+                t0 = time.perf_counter()
+                O.forward_level(x[:s], i) if s < n else O.forward_level(x, i)
+                dt = time.perf_counter() - t0
+                spent += dt
+                timed_levels += 1
+                per = dt * (n / s)
+                last = (i, per)
+            else:
+                per = last[1] * i / last[0]
+            total_est += per * count
+    total = sum(lengths)
+    desc = (f"oracle per-window FFT path (FP64, C, OpenMP); {timed_levels} (length, level) pairs timed "
+            f"on window-aligned slices of <= 2^20 samples (whole signal when a window is larger), "
+            f"scaled by samples covered, remaining levels extrapolated ~ i; {spent:.1f} s of CPU time")
+    return total / total_est, cores, desc
+
+
+# ---------------------------------------------------------------------- main
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="single_16m")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    lengths, real_input, desc = workload_spec(args.workload)
+    nsamp = sum(lengths)
+    alg_bytes = algorithmic_bytes(lengths, real_input)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        x_np = make_input(args.workload)
+        vals = []
+        for k in range(args.warmup + args.steps):
+            v, cores, sdesc = oracle_sample(lengths, x_np, budget_s=4.0)
+            if k >= args.warmup:
+                vals.append(v)
+        value = statistics.median(vals) / 1e9
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gsamples/s",
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": nsamp / (value * 1e9) * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": args.workload, "desc": desc, "signals": len(lengths),
+                           "samples": nsamp},
+                "cpu_baseline": {"value": value, "unit": "Gsamples/s", "cores": cores,
+                                 "kind": "oracle", "sample": sdesc},
+                "e2e": {"value": value, "unit": "Gsamples/s", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    import numpy as np
+    import torch
+    from paper_1507_02525_gb300 import _lib
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max_over_ranks(v: float) -> float:
+        if world == 1:
+            return v
+        import torch.distributed as dist
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    x_np = make_input(args.workload)
+    plan = _lib.Plan(lengths, len(lengths), real_input=real_input, graph=True)
+    info = plan.info()
+    xt = torch.from_numpy(x_np).to(dev)
+    y = torch.empty(plan.out_elems, dtype=torch.complex64, device=dev)
+    gx = torch.empty(plan.in_elems, dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    def fwd():
+        plan.forward(xt.data_ptr(), y.data_ptr(), sp)
+
+    def adj():
+        plan.adjoint(y.data_ptr(), gx.data_ptr(), sp)
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize(dev)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        return max_over_ranks(e0.elapsed_time(e1) / steps)
+
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        gpu_id = gpu_id if gpu_id.startswith("GPU-") else f"GPU-{gpu_id}"
+    except Exception:
+        gpu_id = str(local)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    ms_fwd = timed(fwd, args.steps, args.warmup)
+    ms_adj = timed(adj, args.steps, args.warmup)
+    clk = clocks.stop()
+    plan.status_poll()
+
+    # per-kernel device time (events around each launch on the launch stream)
+    plan.timing_enable(True)
+    for _ in range(2):
+        fwd()
+    kf = plan.timing_read()
+    plan.timing_enable(True)
+    for _ in range(2):
+        adj()
+    ka = plan.timing_read()
+    plan.timing_enable(False)
+
+    peak, peak_src = measured_peaks()
+
+    def dominant(kt, total_ms_per_step):
+        name, (ms, n, b) = max(kt.items(), key=lambda kv: kv[1][0])
+        per_launch_ms = ms / n
+        bytes_per_launch = b / n
+        ach = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9 if bytes_per_launch else 0.0
+        traffic = ncu_traffic(name, args.workload)
+        share = ms / sum(v[0] for v in kt.values())
+        return {"bound": "hbm", "kernel": f"k_{name}", "achieved": round(ach, 1), "peak": peak,
+                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": traffic,
+                "alg_bytes_per_launch": int(bytes_per_launch), "ms_per_launch": round(per_launch_ms, 4),
+                "share_of_step": round(share, 3), "peak_source": peak_src,
+                "per_kernel_ms": {k: round(v[0] / 2, 4) for k, v in kt.items()}}
+
+    roof_fwd = dominant(kf, ms_fwd)
+    roof_adj = dominant(ka, ms_adj)
+    value = world * nsamp / (ms_fwd * 1e-3) / 1e9
+    value_adj = world * nsamp / (ms_adj * 1e-3) / 1e9
+    step_frac = alg_bytes / (ms_fwd * 1e-3) / 1e9 / peak
+    step_frac_adj = alg_bytes / (ms_adj * 1e-3) / 1e9 / peak
+
+    # end to end through the C ABI with host buffers (H2D + transform + D2H)
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x_np).pin_memory()
+        yh = torch.empty(plan.out_elems, dtype=torch.complex64).pin_memory()
+        s2 = torch.cuda.Stream(dev)
+        for _ in range(2):
+            plan.forward_host(xh.data_ptr(), yh.data_ptr(), s2.cuda_stream)
+        e2e_steps = max(3, min(args.steps, 10))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            plan.forward_host(xh.data_ptr(), yh.data_ptr(), s2.cuda_stream)
+        dt = (time.perf_counter() - t0) / e2e_steps
+        dt = max_over_ranks(dt)
+        e2e = {"value": world * nsamp / dt / 1e9, "unit": "Gsamples/s", "ms_per_step": dt * 1e3,
+               "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
+               "d2h_bytes_per_step": int(yh.numel() * yh.element_size()),
+               "api": "mrdft_forward_host (pinned host buffers)"}
+        del xh, yh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sdesc = oracle_sample(lengths, x_np, budget_s=15.0)
+        cpu = {"value": v / 1e9, "unit": "Gsamples/s", "cores": cores, "kind": "oracle", "sample": sdesc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 4), "unit": "Gsamples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_fwd, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": desc, "signals": len(lengths),
+                       "samples_per_gpu": nsamp, "alg_bytes_per_step_per_gpu": alg_bytes,
+                       "l2": "inputs and outputs larger than L2 (no flush needed)" if alg_bytes > 2e8
+                       else "working set smaller than L2",
+                       "parallelism": f"replicas x{world}", "graph": True,
+                       "kernel_source": kernel_source_hash()},
+            "hbm_frac_step": round(step_frac, 4),
+            "roofline": roof_fwd,
+            "adjoint": {"value": round(value_adj, 4), "unit": "Gsamples/s", "ms_per_step": round(ms_adj, 4),
+                        "hbm_frac_step": round(step_frac_adj, 4), "roofline": roof_adj},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "gpu_launches": int(args.steps * info["fwd_launches"]),
+            "gpu_launches_adjoint": int(args.steps * info["adj_launches"]),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -125,6 +125,35 @@ const char* mrdft_last_error(mrdft_plan_t plan);
 mrdft_status mrdft_plan_info(mrdft_plan_t plan, int32_t* tile_log, int32_t* fwd_launches,
                              int32_t* adj_launches);
 
+/* Kernel kinds for per-kernel timing. */
+enum {
+  MRDFT_KIND_FWD_TILE = 0,   /* levels 1..12 of 4096-sample tiles */
+  MRDFT_KIND_FWD_TINY = 1,   /* signals of length <= 16 */
+  MRDFT_KIND_FWD_WINDOW = 2, /* one level (13 or 14) per window */
+  MRDFT_KIND_FWD_COLS = 3,   /* two-pass levels, cross-chunk pass */
+  MRDFT_KIND_FWD_ROWS = 4,   /* two-pass levels, per-residue pass + even bins */
+  MRDFT_KIND_ADJ_TILE = 5,
+  MRDFT_KIND_ADJ_TINY = 6,
+  MRDFT_KIND_ADJ_WINDOW = 7,
+  MRDFT_KIND_ADJ_ROWS = 8,
+  MRDFT_KIND_ADJ_COLS = 9,
+  MRDFT_KIND_COUNT = 10
+};
+
+/*
+ * mrdft_timing_enable -- when enable != 0, every later kernel launch of this
+ * plan is bracketed by CUDA events recorded on its launch stream (graph replay
+ * is bypassed meanwhile); resets the accumulated counters either way.
+ * mrdft_timing_read -- waits for the recorded events and returns, for one
+ * kernel kind, the summed device milliseconds, the number of launches and the
+ * summed algorithmic bytes of those launches (input read once plus the
+ * outputs the kernel writes; zero for pure intermediate passes) since the
+ * last enable.  Any output pointer may be NULL.
+ */
+mrdft_status mrdft_timing_enable(mrdft_plan_t plan, int enable);
+mrdft_status mrdft_timing_read(mrdft_plan_t plan, int kind, double* ms, int64_t* launches,
+                               int64_t* bytes);
+
 /* Release everything the plan owns.  NULL is ignored. */
 void mrdft_destroy(mrdft_plan_t plan);
 

@@ -30,7 +30,10 @@ STATUS_NAMES = {0: "MRDFT_OK", 1: "MRDFT_EINVAL", 2: "MRDFT_ENOMEM", 3: "MRDFT_E
 # every entry point declared in include/mrdft.h
 EXPORTS = ("mrdft_plan", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
            "mrdft_adjoint", "mrdft_forward_host", "mrdft_status_poll", "mrdft_last_error",
-           "mrdft_plan_info", "mrdft_destroy")
+           "mrdft_plan_info", "mrdft_timing_enable", "mrdft_timing_read", "mrdft_destroy")
+
+KINDS = ("fwd_tile", "fwd_tiny", "fwd_window", "fwd_cols", "fwd_rows",
+         "adj_tile", "adj_tiny", "adj_window", "adj_rows", "adj_cols")
 
 
 class MrdftError(RuntimeError):
@@ -69,10 +72,14 @@ def load(build_if_missing: bool = True):
         lib.mrdft_last_error.restype = ctypes.c_char_p
         lib.mrdft_plan_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int32),
                                         ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)]
+        lib.mrdft_timing_enable.argtypes = [vp, i32]
+        lib.mrdft_timing_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(i64), ctypes.POINTER(i64)]
         lib.mrdft_destroy.argtypes = [vp]
         lib.mrdft_destroy.restype = None
         for name in ("mrdft_plan", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
-                     "mrdft_adjoint", "mrdft_forward_host", "mrdft_status_poll", "mrdft_plan_info"):
+                     "mrdft_adjoint", "mrdft_forward_host", "mrdft_status_poll", "mrdft_plan_info",
+                     "mrdft_timing_enable", "mrdft_timing_read"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -131,6 +138,20 @@ class Plan:
     def forward_host(self, x_host_ptr: int, y_host_ptr: int, stream: int = 0) -> None:
         check(self._lib.mrdft_forward_host(self._h, ctypes.c_void_p(x_host_ptr),
                                            ctypes.c_void_p(y_host_ptr), ctypes.c_void_p(stream)), self._h)
+
+    def timing_enable(self, on: bool = True) -> None:
+        check(self._lib.mrdft_timing_enable(self._h, 1 if on else 0), self._h)
+
+    def timing_read(self) -> dict:
+        """{kind: (ms, launches, algorithmic_bytes)} since timing_enable."""
+        out = {}
+        for k, name in enumerate(KINDS):
+            ms, n, b = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+            check(self._lib.mrdft_timing_read(self._h, k, ctypes.byref(ms), ctypes.byref(n),
+                                              ctypes.byref(b)), self._h)
+            if n.value:
+                out[name] = (ms.value, n.value, b.value)
+        return out
 
     def status_poll(self) -> None:
         check(self._lib.mrdft_status_poll(self._h), self._h)

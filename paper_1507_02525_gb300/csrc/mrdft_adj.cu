@@ -87,99 +87,99 @@ __device__ __forceinline__ void adj_chunk_levels_4_1(const AdjArgs& a, const Adj
 }
 
 template <int TLOG, int NT>
-__global__ void __launch_bounds__(NT, 1) k_adj_tile(const AdjArgs a) {
+__global__ void __launch_bounds__(NT, 2) k_adj_tile(const AdjArgs a) {
   constexpr int T = 1 << TLOG;
-  static_assert(T == 32 * NT, "tile = 32 samples per thread");
+  static_assert(T == 16 * NT, "tile = 16 samples per thread");
   extern __shared__ __align__(1024) float2 sm[];
   float2* ACC = sm;                        // T, x_bar accumulator (swz128)
   float2* E[2] = {sm + T, sm + T + T / 2}; // even-bin propagation, level i in E[i & 1]
-  float2* Z = sm + 2 * T;                  // T/2, odd-bin inverse DFT work
-  AdjTileSig* TS = reinterpret_cast<AdjTileSig*>(sm + 2 * T + T / 2);
+  float2* Z = sm + 2 * T;                  // T/2 (pad8), odd-bin inverse DFT work
+  float2* TQ = Z + pad8_size(T / 2);       // quarter-wave w_{2^TLOG} (padded)
+  AdjTileSig* TS = reinterpret_cast<AdjTileSig*>(TQ + twq_size(TLOG));
   const int tid = threadIdx.x;
-  {
-    const int item = blockIdx.x;
-    if (item >= a.nitems) return;
-    const TileItem it = reinterpret_cast<const TileItem*>(a.items)[item];
-    const int tl = it.tlog;
-    const int Tn = it.nsig << tl;
-    const int tn_log = 31 - __clz(Tn);
-    if (tid < it.nsig) {
-      const SigDesc sd = a.sigs[a.sig_ids[it.sig_list + tid]];
-      const int64_t t0 = (int64_t)it.tile << tl;
-      TS[tid] = AdjTileSig{sd.in_off + t0, sd.out_off + t0, sd.m, 0};
-    }
-    // For a tile of a longer signal (one signal, m > tl) the large levels left
-    // contributions in acc and the level-(tl+1) even-bin propagation in e_in.
-    const SigDesc sd0 = a.sigs[a.sig_ids[it.sig_list]];
-    const bool below = sd0.m > tl;
-    __syncthreads();
+  const int item = blockIdx.x;
+  if (item >= a.nitems) return;
+  const TileItem it = reinterpret_cast<const TileItem*>(a.items)[item];
+  const int tl = it.tlog;
+  const int Tn = it.nsig << tl;
+  const int tn_log = 31 - __clz(Tn);
+  if (tid < it.nsig) {
+    const SigDesc sd = a.sigs[a.sig_ids[it.sig_list + tid]];
+    const int64_t t0 = (int64_t)it.tile << tl;
+    TS[tid] = AdjTileSig{sd.in_off + t0, sd.out_off + t0, sd.m, 0};
+  }
+  load_twq<NT>(TQ, TLOG, a.tw);
+  // For a tile of a longer signal (one signal, m > tl) the large levels left
+  // contributions in acc and the level-(tl+1) even-bin propagation in e_in.
+  const SigDesc sd0 = a.sigs[a.sig_ids[it.sig_list]];
+  const bool below = sd0.m > tl;
+  __syncthreads();
+#pragma unroll 4
+  for (int c = tid; c < (Tn >> 1); c += NT) {
+    const int e = c << 1;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (below) v = __ldcg(reinterpret_cast<const float4*>(a.acc + TS[0].x_base + e));
+    st4s_a(ACC + swz128(e), v);
+  }
+
+  // ---- levels tl .. 5 through shared memory
+  const TwQ tw{TQ, TLOG};
+#pragma unroll 1
+  for (int i = tl; i >= 5; --i) {
+    const int L = 1 << i, h = L >> 1;
+    const float2* Ein = E[(i + 1) & 1];
+    float2* Eout = E[i & 1];
+    // G_i = g_i + P_i: even half -> Eout, conj(odd half) -> Z
+#pragma unroll 4
     for (int c = tid; c < (Tn >> 1); c += NT) {
       const int e = c << 1;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (below) v = __ldcg(reinterpret_cast<const float4*>(a.acc + TS[0].x_base + e));
-      st4s_a(ACC + swz128(e), v);
-    }
-
-    // ---- levels tl .. 5 through shared memory
-    static_for<0, TLOG - 4>([&](auto II) MRDFT_INL {
-      constexpr int i = TLOG - decltype(II)::value;  // TLOG, ..., 5
-      constexpr int L = 1 << i, h = L / 2;
-      if (i <= tl) {
-        const float2* Ein = E[(i + 1) & 1];
-        float2* Eout = E[i & 1];
-        // G_i = g_i + P_i: even half -> Eout, conj(odd half) -> Z
-        for (int c = tid; c < (Tn >> 1); c += NT) {
-          const int e = c << 1;
-          const AdjTileSig& ts = TS[e >> tl];
-          const int off = e & ((1 << tl) - 1);
-          float4 g = __ldcs(reinterpret_cast<const float4*>(a.gy + ts.g_base + ((int64_t)(i - 1) << ts.m) + off));
-          const int w = e >> i, k = e & (L - 1);
-          float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (i == tl) {
-            if (below)
-              p = __ldcg(reinterpret_cast<const float4*>(a.e_in + sd0.aux_off + ((int64_t)(it.tile >> 1) << tl) + k));
-          } else {
-            const int pb = ((w >> 1) << i) + k;
-            const float2 pe = Ein[swzf(pb)], po = Ein[swzf(pb + 1)];
-            p = make_float4(pe.x, pe.y, po.x, po.y);
-          }
-          Eout[swzf(w * h + (k >> 1))] = make_float2(g.x + p.x, g.y + p.y);
-          Z[swzf(w * h + (k >> 1))] = make_float2(g.z + p.z, -(g.w + p.w));
-        }
-        __syncthreads();
-        auto src = [&](int b, int n) MRDFT_INL -> float2 { return Z[swzf(b * h + n)]; };
-        auto sink = [&](int b, int n, float2 v) MRDFT_INL {
-          const float2 c = cmulc(conjf2(v), tw_small(a.tw, i, n));  // conj(w^n) zb[n]
-          const int base = b << i;
-          const int i0 = swz128(base + n), i1 = swz128(base + h + n);
-          ACC[i0] = cadd(ACC[i0], c);
-          ACC[i1] = csub(ACC[i1], c);
-        };
-        fft_inplace<i - 1, NT, false>(Z, tn_log - i, a.tw, src, sink);
-        __syncthreads();
-      }
-    });
-
-    // ---- levels 4 .. 1 in registers, two 16-position chunks per thread
-#pragma unroll 1
-    for (int cc = 0; cc < 2; ++cc) {
-      const int chunk = 2 * tid + cc;
-      const int e = chunk << 4;
-      if (e >= Tn) continue;
-      float2 P[16], acc[16];
-#pragma unroll
-      for (int q = 0; q < 16; ++q) {
-        acc[q] = ACC[swz128(e + q)];
-        P[q] = E[1][swzf(((chunk >> 1) << 4) + q)];  // E_5 of the level-5 parent
-      }
       const AdjTileSig& ts = TS[e >> tl];
       const int off = e & ((1 << tl) - 1);
-      adj_chunk_levels_4_1(a, ts, off, P, acc);
-      float4* dst = reinterpret_cast<float4*>(a.gx + ts.x_base + off);
-#pragma unroll
-      for (int q = 0; q < 8; ++q)
-        __stcs(dst + q, make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y));
+      float4 g = __ldcs(reinterpret_cast<const float4*>(a.gy + ts.g_base + ((int64_t)(i - 1) << ts.m) + off));
+      const int w = e >> i, k = e & (L - 1);
+      float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i == tl) {
+        if (below)
+          p = __ldcg(reinterpret_cast<const float4*>(a.e_in + sd0.aux_off + ((int64_t)(it.tile >> 1) << tl) + k));
+      } else {
+        const int pb = ((w >> 1) << i) + k;
+        const float2 pe = Ein[swzf(pb)], po = Ein[swzf(pb + 1)];
+        p = make_float4(pe.x, pe.y, po.x, po.y);
+      }
+      Eout[swzf(w * h + (k >> 1))] = make_float2(g.x + p.x, g.y + p.y);
+      Z[pad8(w * h + (k >> 1))] = make_float2(g.z + p.z, -(g.w + p.w));
     }
+    __syncthreads();
+    auto src = [&](int b, int n) MRDFT_INL -> float2 { return Z[pad8((b << (i - 1)) + n)]; };
+    auto sink = [&](int, int b, int n, float2 v) MRDFT_INL {
+      const float2 c = cmulc(conjf2(v), twq_l(tw, i, n));  // conj(w^n) zb[n]
+      const int base = b << i;
+      const int i0 = swz128(base + n), i1 = swz128(base + h + n);
+      ACC[i0] = cadd(ACC[i0], c);
+      ACC[i1] = csub(ACC[i1], c);
+    };
+    cg_fft<4, TLOG - 1, NT, 8, false, false>(Z, i - 1, tn_log - i, tw, src, NoPre{}, sink);
+    __syncthreads();
+  }
+
+  // ---- levels 4 .. 1 in registers, one 16-position chunk per thread
+  {
+    const int chunk = tid;
+    const int e = chunk << 4;
+    if (e >= Tn) return;
+    float2 P[16], acc[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      acc[q] = ACC[swz128(e + q)];
+      P[q] = E[1][swzf(((chunk >> 1) << 4) + q)];  // E_5 of the level-5 parent
+    }
+    const AdjTileSig& ts = TS[e >> tl];
+    const int off = e & ((1 << tl) - 1);
+    adj_chunk_levels_4_1(a, ts, off, P, acc);
+    float4* dst = reinterpret_cast<float4*>(a.gx + ts.x_base + off);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      __stcs(dst + q, make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y));
   }
 }
 
@@ -224,34 +224,34 @@ __device__ __forceinline__ void acc_add(const AdjArgs& a, const SigDesc& sd, int
   __stcg(p, c);
 }
 
-template <int LB>
-__device__ __forceinline__ void adj_window_level(const AdjArgs& a, const LevelItem& it, float2* Z) {
+__global__ void __launch_bounds__(kWinThreads) k_adj_window(const AdjArgs a) {
   constexpr int NT = kWinThreads;
-  constexpr int h = 1 << LB;
-  const int i = LB + 1;
+  extern __shared__ __align__(1024) float2 sm[];
+  float2* Z = sm;                               // pad8
+  float2* TQ = sm + pad8_size(1 << kWinMaxLog);
+  if (blockIdx.x >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  const int i = a.level;
+  const int LB = i - 1;
+  const int h = 1 << LB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
+  load_twq<NT>(TQ, kWinMaxLog, a.tw);
   for (int k = threadIdx.x; k < h; k += NT) {
     const float4 g = adj_G(a, sd, i, w, 2 * (int64_t)k);
     __stcg(a.e_out + sd.aux_off + (w << LB) + k, make_float2(g.x, g.y));
-    Z[swzf(k)] = make_float2(g.z, -g.w);
+    Z[pad8(k)] = make_float2(g.z, -g.w);
   }
   __syncthreads();
+  const TwQ tw{TQ, kWinMaxLog};
   const int64_t ws = w << i;
-  auto src = [&](int, int n) -> float2 { return Z[swzf(n)]; };
-  auto sink = [&](int, int n, float2 v) MRDFT_INL {
+  auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[pad8(n)]; };
+  auto sink = [&](int, int, int n, float2 v) MRDFT_INL {
     const float2 c = cmulc(conjf2(v), tw_any(a.tw, i, n));
     acc_add(a, sd, i, ws + n, c);
     acc_add(a, sd, i, ws + h + n, make_float2(-c.x, -c.y));
   };
-  fft_inplace<LB, NT, false>(Z, 0, a.tw, src, sink);
-}
-
-template <int LB>
-__global__ void __launch_bounds__(kWinThreads) k_adj_window(const AdjArgs a) {
-  extern __shared__ __align__(1024) float2 sm[];
-  if (blockIdx.x >= a.nitems) return;
-  adj_window_level<LB>(a, reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x], sm);
+  cg_fft<kTileLog, kWinMaxLog, NT, 32, false, false>(Z, LB, 0, tw, src, NoPre{}, sink);
 }
 
 // =============================================================== two-pass
@@ -260,116 +260,95 @@ __global__ void __launch_bounds__(kWinThreads) k_adj_window(const AdjArgs a) {
 // rows: item (sig, window, block) covers residues k2 in [k0, k0 + 4):
 //   G odd bins k = Q k1 + k2 -> IDFT_C over k1 -> times conj(w_h^(r k2))
 //   -> scratch U[window][k2][r]; even bins -> e_out.
-template <int QB>
-__device__ __forceinline__ void adj_rows_level(const AdjArgs& a, const LevelItem& it, float2* S) {
+__global__ void __launch_bounds__(kPassThreads) k_adj_rows(const AdjArgs a) {
   constexpr int NT = kPassThreads;
   constexpr int CB = kColsLog, C = 1 << CB;
   constexpr int KCB = 14 - CB, KC = 1 << KCB;
-  constexpr int HB = QB + CB;
-  const int i = HB + 1;
+  extern __shared__ __align__(1024) float2 sm[];
+  float2* S = sm;                               // sequence j at j C (pad8)
+  float2* TQ = sm + pad8_size(kPassElems);
+  if (blockIdx.x >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  const int i = a.level;
+  const int HB = i - 1, QB = HB - CB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
   const int k0 = it.block << KCB;
+  load_twq<NT>(TQ, CB, a.tw);
   for (int e = threadIdx.x; e < KC * C; e += NT) {
     const int j = e & (KC - 1), k1 = e >> KCB;
     const int64_t k = ((int64_t)k1 << QB) + k0 + j;
     const float4 g = adj_G(a, sd, i, w, 2 * k);
     __stcg(a.e_out + sd.aux_off + (w << HB) + k, make_float2(g.x, g.y));
-    S[swzf((j << CB) + k1)] = make_float2(g.z, -g.w);
+    S[pad8((j << CB) + k1)] = make_float2(g.z, -g.w);
   }
   __syncthreads();
+  const TwQ tw{TQ, CB};
   float2* U = a.scratch + sd.aux_off + (w << HB);
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((b << CB) + n)]; };
-  auto sink = [&](int b, int r, float2 v) MRDFT_INL {
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[pad8((b << CB) + n)]; };
+  auto sink = [&](int, int b, int r, float2 v) MRDFT_INL {
     const int k2 = k0 + b;
     __stcg(U + ((int64_t)k2 << CB) + r, cmulc(conjf2(v), tw_any(a.tw, HB, (int64_t)r * k2)));
   };
-  fft_inplace<CB, NT, false>(S, KCB, a.tw, src, sink);
-}
-
-template <int QB>
-__global__ void __launch_bounds__(kPassThreads) k_adj_rows(const AdjArgs a) {
-  extern __shared__ __align__(1024) float2 sm[];
-  if (blockIdx.x >= a.nitems) return;
-  adj_rows_level<QB>(a, reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x], sm);
+  cg_fft<CB, CB, NT, 32, false, false>(S, CB, KCB, tw, src, NoPre{}, sink);
 }
 
 // cols: item (sig, window, block) covers chunk offsets r in [r0, r0 + RC):
 //   U[window][k2][r] -> IDFT_Q over k2 -> zb[r + C q] -> conj(w_{2^i}^n) zb
 //   added to acc at n and subtracted at h + n.
-template <int QB>
-__device__ __forceinline__ void adj_cols_level(const AdjArgs& a, const LevelItem& it, float2* S) {
+__global__ void __launch_bounds__(kPassThreads) k_adj_cols(const AdjArgs a) {
   constexpr int NT = kPassThreads;
-  constexpr int CB = kColsLog, C = 1 << CB;
-  constexpr int Q = 1 << QB;
-  constexpr int RCB = 14 - QB, RC = 1 << RCB;
-  constexpr int HB = QB + CB;
-  constexpr int64_t h = (int64_t)1 << HB;
-  const int i = HB + 1;
+  constexpr int CB = kColsLog;
+  extern __shared__ __align__(1024) float2 sm[];
+  float2* S = sm;                               // column r position k2 at k2 RC + r (pad8)
+  float2* TQ = sm + pad8_size(kPassElems);
+  if (blockIdx.x >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  const int i = a.level;
+  const int HB = i - 1, QB = HB - CB;
+  const int RCB = 14 - QB, RC = 1 << RCB;
+  const int Q = 1 << QB;
+  const int64_t h = (int64_t)1 << HB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
   const int r0 = it.block << RCB;
   const float2* U = a.scratch + sd.aux_off + (w << HB);
+  load_twq<NT>(TQ, kWinMaxLog, a.tw);
+#pragma unroll 4
   for (int e = threadIdx.x; e < RC * Q; e += NT) {
     const int r = e & (RC - 1), k2 = e >> RCB;
-    S[swzf((r << QB) + k2)] = conjf2(__ldcg(U + ((int64_t)k2 << CB) + r0 + r));
+    S[pad8(e)] = conjf2(__ldcg(U + ((int64_t)k2 << CB) + r0 + r));  // e = k2 RC + r
   }
   __syncthreads();
+  // this block's columns of the intermediate are dead: drop them from L2
+  if (RC >= 16)
+    for (int l = threadIdx.x; l < Q * (RC / 16); l += NT)
+      discard_l2(U + ((int64_t)(l / (RC / 16)) << CB) + r0 + 16 * (l % (RC / 16)));
+  const TwQ tw{TQ, kWinMaxLog};
   const int64_t ws = w << i;
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((b << QB) + n)]; };
-  auto sink = [&](int b, int q, float2 v) MRDFT_INL {
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[pad8((n << RCB) + b)]; };
+  auto sink = [&](int, int b, int q, float2 v) MRDFT_INL {
     const int64_t n = ((int64_t)q << CB) + r0 + b;
     const float2 c = cmulc(conjf2(v), tw_any(a.tw, i, n));
     acc_add(a, sd, i, ws + n, c);
     acc_add(a, sd, i, ws + h + n, make_float2(-c.x, -c.y));
   };
-  fft_inplace<QB, NT, true>(S, RCB, a.tw, src, sink);
-}
-
-template <int QB>
-__global__ void __launch_bounds__(kPassThreads) k_adj_cols(const AdjArgs a) {
-  extern __shared__ __align__(1024) float2 sm[];
-  if (blockIdx.x >= a.nitems) return;
-  adj_cols_level<QB>(a, reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x], sm);
+  cg_fft<2, kWinMaxLog, NT, 32, true, false>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
 // ================================================================ launchers
 
-static constexpr size_t kAdjTileSmem = (size_t)(2 * kTile + kTile / 2) * sizeof(float2) + kAdjMaxPack * sizeof(AdjTileSig);
-static constexpr size_t kAdjWinSmem = (size_t)(1 << kWinMaxLog) * sizeof(float2);
-static constexpr size_t kAdjPassSmem = (size_t)kPassElems * sizeof(float2);
-
-using AdjKernel = void (*)(const AdjArgs);
-static AdjKernel adj_win_kernel(int level) {
-  switch (level) {
-    case 13: return k_adj_window<12>;
-    case 14: return k_adj_window<13>;
-    default: return nullptr;
-  }
-}
-template <int QB>
-static void adj_pass_pair(int level, AdjKernel* r, AdjKernel* c) {
-  if constexpr (QB <= 13) {
-    if (level == QB + kColsLog + 1) {
-      *r = k_adj_rows<QB>;
-      *c = k_adj_cols<QB>;
-      return;
-    }
-    adj_pass_pair<QB + 1>(level, r, c);
-  }
-}
+static constexpr size_t kAdjTileSmem =
+    (size_t)(2 * kTile + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kAdjMaxPack * sizeof(AdjTileSig);
+static constexpr size_t kAdjWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog)) * sizeof(float2);
+static constexpr size_t kAdjPassSmem = (size_t)(pad8_size(kPassElems) + twq_size(kWinMaxLog)) * sizeof(float2);
 
 cudaError_t set_adj_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_adj_tile<kTileLog, kTileThreads>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjTileSmem);
-  for (int lv = 13; lv <= 14 && e == cudaSuccess; ++lv)
-    e = cudaFuncSetAttribute(adj_win_kernel(lv), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
-  for (int lv = 15; lv <= 26 && e == cudaSuccess; ++lv) {
-    AdjKernel r = nullptr, c = nullptr;
-    adj_pass_pair<2>(lv, &r, &c);
-    e = cudaFuncSetAttribute(r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjPassSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjPassSmem);
-  }
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjPassSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjPassSmem);
   return e;
 }
 
@@ -382,23 +361,15 @@ cudaError_t launch_adj_tiny(const AdjArgs& a, int nsig_tiny, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s) {
-  AdjKernel k = adj_win_kernel(a.level);
-  if (!k) return cudaErrorInvalidValue;
-  k<<<grid, kWinThreads, kAdjWinSmem, s>>>(a);
+  k_adj_window<<<grid, kWinThreads, kAdjWinSmem, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s) {
-  AdjKernel r = nullptr, c = nullptr;
-  adj_pass_pair<2>(a.level, &r, &c);
-  if (!r) return cudaErrorInvalidValue;
-  r<<<grid, kPassThreads, kAdjPassSmem, s>>>(a);
+  k_adj_rows<<<grid, kPassThreads, kAdjPassSmem, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_adj_cols(const AdjArgs& a, int grid, cudaStream_t s) {
-  AdjKernel r = nullptr, c = nullptr;
-  adj_pass_pair<2>(a.level, &r, &c);
-  if (!c) return cudaErrorInvalidValue;
-  c<<<grid, kPassThreads, kAdjPassSmem, s>>>(a);
+  k_adj_cols<<<grid, kPassThreads, kAdjPassSmem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -123,12 +123,14 @@ __device__ __forceinline__ void idft_reg(float2 (&v)[R]) {
 }
 
 // ------------------------------------------------------ shared-memory maps
-// Level / input tile buffers: rows of 16 complex (128 B); the 16-B chunk c of
-// row r lives at chunk c ^ (r & 7) -- the 128-byte swizzle a TMA tensor copy
-// with CU_TENSOR_MAP_SWIZZLE_128B produces.  Index in float2 units.
+// Level / input tile buffers: rows of 16 complex (128 B); the 16-byte chunk c
+// (two complex) of row r lives at chunk c ^ ((r ^ r>>3 ^ r>>6) & 7), so that
+// lanes walking rows with any power-of-two stride up to 64 rows, or walking
+// consecutive elements, hit distinct banks.  Index in float2 units; pairs
+// (2q, 2q+1) stay adjacent, so 16-byte vector accesses remain valid.
 __device__ __forceinline__ int swz128(int e) {
-  int r = e >> 4;
-  return (r << 4) | ((((e >> 1) & 7) ^ (r & 7)) << 1) | (e & 1);
+  const int r = e >> 4;
+  return (r << 4) | ((((e >> 1) & 7) ^ ((r ^ (r >> 3) ^ (r >> 6)) & 7)) << 1) | (e & 1);
 }
 // FFT work buffers: XOR the low 4 index bits with bits 4..7 and 8..11 so that
 // power-of-two strides up to 2^12 spread over all banks (8-byte elements).
@@ -159,6 +161,22 @@ __device__ __forceinline__ float2 tw_any(const Twiddles& T, int l, int64_t e) {
   if (l <= kTwLog) return tw_small(T, l, (int)(e & ((1 << l) - 1)));
   uint32_t q = (uint32_t)((e << (kTwBigLog - l)) & ((1 << kTwBigLog) - 1));
   return cmul(__ldg(&T.twhi[q >> kTwSplit]), __ldg(&T.twlo[q & ((1 << kTwSplit) - 1)]));
+}
+
+// ------------------------------------------------------------ async copies
+// 16-byte global -> shared copy that bypasses registers (cp.async, L2 only).
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+// Invalidate one 128-byte L2 line without writing it back (dead scratch).
+// p must be 128-byte aligned.
+__device__ __forceinline__ void discard_l2(const void* p) {
+  asm volatile("discard.global.L2 [%0], 128;\n" ::"l"(p) : "memory");
 }
 
 // ------------------------------------------------------------ status word

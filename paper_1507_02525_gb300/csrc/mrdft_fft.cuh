@@ -1,110 +1,206 @@
 // Shared-memory FFT engine used by every MrDFT kernel for the odd-bin DFTs
 // (the F^(i) / R^(i) step of Sec. 3 of Andreatto & Cariow, there a radix-2
-// decimation-in-frequency FFT with bit-reversed output).  Here the same DFT
-// is taken in radix-16 passes (remainder radix last), in place, over `nseq`
-// independent sequences of length L = 2^LB held in one shared buffer; the
-// bit-reversed order is undone by the thread mapping of the last pass, so the
-// sink receives bins in natural order with consecutive lanes on consecutive
-// bins.
+// decimation-in-frequency FFT with bit-reversed output).
+//
+// Here the same DFT runs as a constant-geometry decimation-in-time FFT (the
+// transpose of a constant-geometry DIF factorisation): the input is read in
+// digit-reversed order by the first pass, and every pass then reads 2^RB
+// consecutive elements per group and writes them at a fixed stride L / 2^RB,
+// so the last pass emits bins in natural order with consecutive lanes on
+// consecutive bins.  All radices are 8 except the first pass (2, 4 or 8).
+//
+// Shared layout: element a of the work buffer lives at pad8(a) = a + a/8, so
+// both the 8-consecutive reads and the lane-consecutive strided writes are
+// free of bank conflicts and their addresses are a base plus constants.
+// Sequences are stored sequence-major (b * L + pos) or, SEQ_MINOR,
+// position-major (pos * nseq + b, consecutive lanes on consecutive sequences).
 #pragma once
 #include "mrdft_common.cuh"
 
 namespace mrdft {
 
-// reverse D hexadecimal digits of v
-template <int D>
-__device__ __forceinline__ int drev16(int v) {
-  if constexpr (D <= 1) return v;
-  else if constexpr (D == 2) return ((v & 15) << 4) | (v >> 4);
-  else if constexpr (D == 3) return ((v & 15) << 8) | (v & 0xF0) | (v >> 8);
-  else return ((v & 15) << 12) | ((v & 0xF0) << 4) | ((v >> 4) & 0xF0) | (v >> 12);
+__device__ __forceinline__ int pad8(int a) { return a + (a >> 3); }
+__host__ __device__ constexpr int pad8_size(int n) { return n + n / 8; }
+
+// Twiddles w_{2^TB}^e from a quarter-wave table q[r] = w_{2^TB}^r, r < 2^(TB-2)
+// (FP64 values rounded once), using w^(r + s 2^(TB-2)) = (-j)^s w^r.  The
+// table is stored padded (entry r at r + r/16 + r/256) so that lanes reading
+// exponents with a power-of-two stride hit distinct banks.
+struct TwQ {
+  const float2* q;
+  int TB;
+};
+__device__ __forceinline__ int twq_pad(int r) { return r + (r >> 4) + (r >> 8); }
+__host__ __device__ constexpr int twq_size(int TB) {
+  return (1 << (TB - 2)) + (1 << (TB - 6)) + (1 << (TB - 10)) + 1;
+}
+__device__ __forceinline__ float2 twq(const TwQ& t, int e) {
+  const int qb = t.TB - 2;
+  const float2 w = t.q[twq_pad(e & ((1 << qb) - 1))];
+  // times (-j)^s for the quadrant s, branch-free: swap re/im for odd s, then
+  // sign flips (re for s = 2, 3; im for s = 1, 2)
+  const int s = (e >> qb) & 3;
+  const float a = (s & 1) ? w.y : w.x;
+  const float b = (s & 1) ? w.x : w.y;
+  const unsigned sre = (unsigned)(s & 2) << 30;
+  const unsigned sim = (unsigned)((s ^ (s >> 1)) & 1) << 31;
+  return make_float2(__uint_as_float(__float_as_uint(a) ^ sre), __uint_as_float(__float_as_uint(b) ^ sim));
+}
+// w_{2^l}^e for l <= TB
+__device__ __forceinline__ float2 twq_l(const TwQ& t, int l, int e) { return twq(t, e << (t.TB - l)); }
+
+// w^(k * step), k = 0 .. R-1, from log2(R) table entries (w^step, w^2step,
+// w^4step) and products of them (at most two extra roundings).
+template <int R>
+__device__ __forceinline__ void twiddle_set(const TwQ& tw, int step, float2 (&w)[R]) {
+  w[0] = make_float2(1.f, 0.f);
+  if constexpr (R >= 2) w[1] = twq(tw, step);
+  if constexpr (R >= 4) {
+    w[2] = twq(tw, 2 * step);
+    w[3] = cmul(w[1], w[2]);
+  }
+  if constexpr (R >= 8) {
+    w[4] = twq(tw, 4 * step);
+    w[5] = cmul(w[4], w[1]);
+    w[6] = cmul(w[4], w[2]);
+    w[7] = cmul(w[4], w[3]);
+  }
 }
 
-// In-place forward DFT of nseq = 2^nseq_log sequences of length 2^LB.
-//   Z      : work buffer, element p of sequence b at Z[swzf(b * L + p)]
-//   src    : float2 src(int b, int n) -- input sample n of sequence b (first pass)
-//   sink   : void sink(int b, int k, float2 v) -- bin k (natural order) of b
-//   SEQ_FAST: consecutive threads walk sequences first (for sinks that store
-//            one bin of many sequences contiguously), else bins first.
-// All NT threads of the block must call it; it synchronises between passes
-// but not before the first or after the last.
-template <int LB, int NT, bool SEQ_FAST, class Src, class Sink>
-__device__ __forceinline__ void fft_inplace(float2* __restrict__ Z, int nseq_log,
-                                            const Twiddles& T, Src&& src, Sink&& sink) {
-  constexpr int L = 1 << LB;
-  constexpr int P = (LB + 3) / 4;
+// reverse the d low octal digits of v
+__device__ __forceinline__ int drev8(int v, int d) {
+  int r = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+    if (i < d) r |= ((v >> (3 * i)) & 7) << (3 * (d - 1 - i));
+  return r;
+}
+
+// One pass of the constant-geometry DIT FFT.
+//   LB: log2 sequence length; nseq_log: log2 number of sequences;
+//   RB: log2 radix of this pass; SH: 3 * (DIF pass index) -- the twiddle of
+//   input r of group g is w_M^((g >> SH) r) with M = L >> SH; P: pass count.
+//   FIRST: inputs come from src(b, n) in natural index n (the digit reversal
+//   is folded into the index); LAST: outputs go to sink(slot, b, k, v) with
+//   bin k natural; PRE: pre(slot, b, k) runs for every output bin before a
+//   barrier that separates every read of this pass from the sink's writes.
+// Every thread loads all its groups before the pass's barrier, so the pass is
+// in place; PTS bounds the points per thread (NT * PTS >= points per pass).
+template <int RB, int NT, int PTS, bool SEQ_MINOR, bool FIRST, bool LAST, bool PRE, class Src, class Pre, class Sink>
+__device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq_log, int SH, int P, const TwQ& tw,
+                                        Src&& src, Pre&& pre, Sink&& sink) {
+  constexpr int R = 1 << RB;
+  constexpr int GMAX = (PTS >> RB) > 0 ? (PTS >> RB) : 1;  // groups per thread
+  const int LRB = LB - RB;                      // log2(L / R): groups per sequence
+  const int ngroups = 1 << (nseq_log + LRB);
   const int tid = threadIdx.x;
-  static_for<0, P>([&](auto PP) MRDFT_INL {
-    constexpr int p = decltype(PP)::value;
-    constexpr int rb = (p < LB / 4) ? 4 : (LB % 4);
-    constexpr int R = 1 << rb;
-    constexpr int MB = LB - 4 * p;  // log2 of the sub-problem length at this pass
-    constexpr int M = 1 << MB;
-    constexpr int MR = M / R;
-    constexpr int GPT = 16 / R;     // groups per thread per round (16 points)
-    constexpr int LR_LOG = LB - rb; // log2(L / R)
-    constexpr bool FIRST = (p == 0), LAST = (p == P - 1);
-    const int ngroups = 1 << (nseq_log + LR_LOG);
-#pragma unroll 1
-    for (int base = 0; base < ngroups; base += NT * GPT) {
-      float2 v[GPT][R];
-      int gb[GPT], gr[GPT];
+  float2 v[GMAX][R];
 #pragma unroll
-      for (int j = 0; j < GPT; ++j) {
-        const int g = base + tid + j * NT;
-        int b, r;
-        if constexpr (SEQ_FAST) {
-          b = g & ((1 << nseq_log) - 1);
-          r = g >> nseq_log;
-        } else {
-          b = g >> LR_LOG;
-          r = g & ((1 << LR_LOG) - 1);
-        }
-        gb[j] = b;
-        gr[j] = r;
-        if (g < ngroups) {
-          // sub-problem u, offset n2 inside it
-          int u, n2;
-          if constexpr (LAST && P > 1) {
-            u = drev16<P - 1>(r);
-            n2 = 0;
-          } else {
-            u = r / MR;
-            n2 = r % MR;
-          }
-          const int pos0 = u * M + n2;
-#pragma unroll
-          for (int n1 = 0; n1 < R; ++n1) {
-            const int pos = pos0 + n1 * MR;
-            if constexpr (FIRST) v[j][n1] = src(b, pos);
-            else v[j][n1] = Z[swzf((b << LB) + pos)];
-          }
-        }
+  for (int j = 0; j < GMAX; ++j) {
+    const int G = tid + j * NT;
+    if (G < ngroups) {
+      int b, g;
+      if constexpr (SEQ_MINOR) {
+        b = G & ((1 << nseq_log) - 1);
+        g = G >> nseq_log;
+      } else {
+        b = G >> LRB;
+        g = G & ((1 << LRB) - 1);
       }
+      if constexpr (FIRST) {
+        // position R g + r holds natural index drev8(g) + (L / R) r
+        const int n0 = drev8(g, P - 1);
 #pragma unroll
-      for (int j = 0; j < GPT; ++j) {
-        const int g = base + tid + j * NT;
-        if (g >= ngroups) continue;
-        dft_reg<R>(v[j]);
-        if constexpr (!LAST) {
-          const int n2 = gr[j] % MR;
-          if (n2 != 0) {
+        for (int r = 0; r < R; ++r) v[j][r] = src(b, n0 + (r << LRB));
+      } else {
+        const int a0 = SEQ_MINOR ? (((g << RB) << nseq_log) + b) : ((b << LB) + (g << RB));
 #pragma unroll
-            for (int k1 = 1; k1 < R; ++k1) v[j][k1] = cmul(v[j][k1], tw_small(T, MB, n2 * k1));
-          }
-          const int u = gr[j] / MR;
-          const int pos0 = u * M + n2;
+        for (int r = 0; r < R; ++r) v[j][r] = Z[pad8(a0 + (SEQ_MINOR ? (r << nseq_log) : r))];
+      }
+      const int tg = g >> SH;
+      if (tg != 0) {
+        float2 w[R];
+        twiddle_set<R>(tw, tg << (tw.TB - (LB - SH)), w);  // w_M^(tg r)
 #pragma unroll
-          for (int k1 = 0; k1 < R; ++k1) Z[swzf((gb[j] << LB) + pos0 + k1 * MR)] = v[j][k1];
-        } else {
-          // bins: k = l + (L / R) * k1 with l = r (digit-reversed sub-problem)
+        for (int r = 1; r < R; ++r) v[j][r] = cmul(v[j][r], w[r]);
+      }
+      if constexpr (LAST && PRE) {
 #pragma unroll
-          for (int k1 = 0; k1 < R; ++k1) sink(gb[j], gr[j] + k1 * (L / R), v[j][k1]);
-        }
+        for (int k = 0; k < R; ++k) pre(j * R + k, b, g + (k << LRB));
       }
     }
-    if constexpr (!LAST) __syncthreads();
-  });
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < GMAX; ++j) {
+    const int G = tid + j * NT;
+    if (G >= ngroups) continue;
+    int b, g;
+    if constexpr (SEQ_MINOR) {
+      b = G & ((1 << nseq_log) - 1);
+      g = G >> nseq_log;
+    } else {
+      b = G >> LRB;
+      g = G & ((1 << LRB) - 1);
+    }
+    dft_reg<R>(v[j]);
+    if constexpr (LAST) {
+#pragma unroll
+      for (int k = 0; k < R; ++k) sink(j * R + k, b, g + (k << LRB), v[j][k]);
+    } else {
+      const int a0 = SEQ_MINOR ? ((g << nseq_log) + b) : ((b << LB) + g);
+#pragma unroll
+      for (int k = 0; k < R; ++k) Z[pad8(a0 + (SEQ_MINOR ? ((k << LRB) << nseq_log) : (k << LRB)))] = v[j][k];
+    }
+  }
 }
+
+// Full forward DFT of 2^nseq_log sequences of runtime length 2^LB
+// (LBMIN <= LB <= LBMAX, LB >= 1).  Starts with a barrier-free read of src,
+// ends after the sink; synchronises internally.  The caller synchronises
+// before reusing Z or reading what the sink wrote.
+//   src(b, n) -> float2;  pre(slot, b, k) (PRE only);  sink(slot, b, k, v).
+template <int LBMIN, int LBMAX, int NT, int PTS, bool SEQ_MINOR, bool PRE, class Src, class Pre, class Sink>
+__device__ __forceinline__ void cg_fft(float2* __restrict__ Z, int LB, int nseq_log, const TwQ& tw, Src&& src,
+                                       Pre&& pre, Sink&& sink) {
+  const int P = (LB + 2) / 3;
+  const int r0 = LB - 3 * (P - 1);  // radix bits of the first (remainder) pass
+  if (P == 1) {
+    static_for<1, 4>([&](auto RR) MRDFT_INL {
+      constexpr int rb = decltype(RR)::value;
+      if constexpr (rb >= LBMIN && rb <= LBMAX)
+        if (r0 == rb)
+          cg_pass<rb, NT, PTS, SEQ_MINOR, true, true, PRE>(Z, LB, nseq_log, LB, 1, tw, src, pre, sink);
+    });
+    return;
+  }
+  if constexpr (LBMAX >= 4) {
+    static_for<1, 4>([&](auto RR) MRDFT_INL {
+      constexpr int rb = decltype(RR)::value;
+      if (r0 == rb)
+        cg_pass<rb, NT, PTS, SEQ_MINOR, true, false, false>(Z, LB, nseq_log, 3 * (P - 1), P, tw, src, pre, sink);
+    });
+#pragma unroll 1
+    for (int p = P - 2; p >= 1; --p) {
+      __syncthreads();
+      cg_pass<3, NT, PTS, SEQ_MINOR, false, false, false>(Z, LB, nseq_log, 3 * p, P, tw, src, pre, sink);
+    }
+    __syncthreads();
+    cg_pass<3, NT, PTS, SEQ_MINOR, false, true, PRE>(Z, LB, nseq_log, 0, P, tw, src, pre, sink);
+  }
+}
+
+// Fill a quarter-wave table of w_{2^TB} in shared memory from the global
+// FP64-rounded-once table w_{2^13}^e (TB <= 13).
+template <int NT>
+__device__ __forceinline__ void load_twq(float2* q, int TB, const Twiddles& T) {
+  const int n = 1 << (TB - 2);
+  for (int r = threadIdx.x; r < n; r += NT) q[twq_pad(r)] = __ldg(&T.tw13[r << (kTwLog - TB)]);
+}
+
+// no-op pre-sink
+struct NoPre {
+  __device__ __forceinline__ void operator()(int, int, int) const {}
+};
 
 }  // namespace mrdft

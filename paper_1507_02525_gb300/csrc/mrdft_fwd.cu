@@ -51,6 +51,7 @@ struct TileSig {
   int32_t pad;
 };
 constexpr int kMaxPack = kTile / 32;  // signals of >= 32 samples per tile
+static_assert(sizeof(TileSig) == 24, "TileSig layout");
 
 // Levels 1..4 of one 16-sample chunk (one 128-byte row of the tile), in
 // registers: A^(1), then U / V / D / F per level with compile-time twiddles.
@@ -109,72 +110,83 @@ __device__ __forceinline__ void tile_chunk_levels_1_4(const FwdArgs& a, const fl
 }
 
 template <int TLOG, int NT>
-__global__ void __launch_bounds__(NT, 1) k_fwd_tile(const FwdArgs a) {
+__global__ void __launch_bounds__(NT, 2) k_fwd_tile(const FwdArgs a) {
   constexpr int T = 1 << TLOG;
-  static_assert(T == 32 * NT, "tile = 32 samples per thread");
+  static_assert(T == 16 * NT, "tile = 16 samples per thread");
   extern __shared__ __align__(1024) float2 sm[];
-  float2* X = sm;
-  float2* B[2] = {sm + T, sm + 2 * T};  // level i lives in B[i & 1]
-  float2* Z = sm + 3 * T;
-  TileSig* TS = reinterpret_cast<TileSig*>(sm + 3 * T + T / 2);
+  float2* X = sm;                       // x tile (swz128)
+  float2* B = sm + T;                   // current level, updated in place (swz128)
+  float2* Z = sm + 2 * T;               // odd-bin DFT work area (pad8)
+  float2* TQ = Z + pad8_size(T / 2);    // quarter-wave w_{2^TLOG} (padded)
+  TileSig* TS = reinterpret_cast<TileSig*>(TQ + twq_size(TLOG));
   const int tid = threadIdx.x;
+  const int item = blockIdx.x;
+  if (item >= a.nitems) return;
+  const TileItem it = reinterpret_cast<const TileItem*>(a.items)[item];
+  const int tl = it.tlog;
+  const int Tn = it.nsig << tl;
+  const int tn_log = 31 - __clz(Tn);
+  if (tid < it.nsig) {
+    const SigDesc sd = a.sigs[a.sig_ids[it.sig_list + tid]];
+    const int64_t t0 = (int64_t)it.tile << tl;
+    TS[tid] = TileSig{sd.in_off + t0, sd.out_off + t0, sd.m, 0};
+  }
+  load_twq<NT>(TQ, TLOG, a.tw);
+  __syncthreads();
 
-  {
-    // one work item per CTA: a persistent loop lets the compiler hoist the
-    // per-level address arithmetic out of it and spill
-    const int item = blockIdx.x;
-    if (item >= a.nitems) return;
-    const TileItem it = reinterpret_cast<const TileItem*>(a.items)[item];
-    const int tl = it.tlog;
-    const int Tn = it.nsig << tl;
-    const int tn_log = 31 - __clz(Tn);
-    if (tid < it.nsig) {
-      const SigDesc sd = a.sigs[a.sig_ids[it.sig_list + tid]];
-      const int64_t t0 = (int64_t)it.tile << tl;
-      TS[tid] = TileSig{sd.in_off + t0, sd.out_off + t0, sd.m, 0};
+  // ---- stage the tile of x (P^(1): x is read once and reused per level)
+  if (!a.in_real) {
+    const float2* xg = reinterpret_cast<const float2*>(a.x);
+#pragma unroll 4
+    for (int c = tid; c < (Tn >> 1); c += NT) {
+      const int e = c << 1;
+      cp_async16(X + swz128(e), xg + TS[e >> tl].in_base + (e & ((1 << tl) - 1)));
     }
-    __syncthreads();
-
-    // ---- stage the tile of x (P^(1): x is read once and reused per level)
+    cp_async_wait_all();
+  } else {
+#pragma unroll 4
     for (int c = tid; c < (Tn >> 1); c += NT) {
       const int e = c << 1;
       st4s(X + swz128(e), load_x2(a, TS[e >> tl].in_base + (e & ((1 << tl) - 1))));
     }
-    __syncthreads();
+  }
+  __syncthreads();
 
-    // ---- levels 1..4 in registers, two 16-sample chunks per thread
+  // ---- levels 1..4 in registers, one 16-sample chunk per thread
+  {
+    const int e = tid << 4;
+    if (e < Tn) tile_chunk_levels_1_4(a, X, B, tid, TS[e >> tl], e & ((1 << tl) - 1));
+  }
+  __syncthreads();
+
+  // ---- levels 5..tlog through the shared-memory FFT engine; B is updated in
+  // place: every child read (pre) happens before the barrier in the last pass
+  const TwQ tw{TQ, TLOG};
 #pragma unroll 1
-    for (int cc = 0; cc < 2; ++cc) {
-      const int chunk = 2 * tid + cc;
-      const int e = chunk << 4;
-      if (e < Tn) tile_chunk_levels_1_4(a, X, B[0], chunk, TS[e >> tl], e & ((1 << tl) - 1));
-    }
+  for (int i = 5; i <= tl; ++i) {
+    const int h = 1 << (i - 1);
+    const bool keep = i < tl;  // the next level reads this one
+    float2 ev[8];
+    auto src = [&](int b, int n) MRDFT_INL -> float2 {
+      const int base = b << i;
+      return cmul(csub(X[swz128(base + n)], X[swz128(base + h + n)]), twq_l(tw, i, n));
+    };
+    auto pre = [&](int slot, int b, int k) MRDFT_INL {
+      const int base = b << i;
+      ev[slot] = cadd(B[swz128(base + k)], B[swz128(base + h + k)]);  // U: child sum
+    };
+    auto sink = [&](int slot, int b, int k, float2 odd) MRDFT_INL {
+      const int e = (b << i) + 2 * k;
+      const float4 v = make_float4(ev[slot].x, ev[slot].y, odd.x, odd.y);
+      if (keep) st4s(B + swz128(e), v);
+      const TileSig& ts = TS[e >> tl];
+      float4* dst = reinterpret_cast<float4*>(a.y + ts.out_base + ((int64_t)(i - 1) << ts.m) + (e & ((1 << tl) - 1)));
+      // the tile's top level is re-read (children of level tl+1): keep it in L2
+      if (i == tl && ts.m > tl) __stcg(dst, v);
+      else __stcs(dst, v);
+    };
+    cg_fft<4, TLOG - 1, NT, 8, false, true>(Z, i - 1, tn_log - i, tw, src, pre, sink);
     __syncthreads();
-
-    // ---- levels 5..tlog through the shared-memory FFT engine
-    static_for<5, TLOG + 1>([&](auto I) MRDFT_INL {
-      constexpr int i = decltype(I)::value;
-      constexpr int L = 1 << i, h = L / 2;
-      if (i <= tl) {
-        const float2* Bp = B[(i - 1) & 1];
-        float2* Bc = B[i & 1];
-        const bool keep = i < tl;  // the next level reads this one
-        auto src = [&](int b, int n) MRDFT_INL -> float2 {
-          const int base = b << i;
-          return cmul(csub(X[swz128(base + n)], X[swz128(base + h + n)]), tw_small(a.tw, i, n));
-        };
-        auto sink = [&](int b, int k, float2 odd) MRDFT_INL {
-          const int e = (b << i) + 2 * k;
-          const float2 ev = cadd(Bp[swz128((b << i) + k)], Bp[swz128((b << i) + h + k)]);
-          const float4 v = make_float4(ev.x, ev.y, odd.x, odd.y);
-          if (keep) st4s(Bc + swz128(e), v);
-          const TileSig& ts = TS[e >> tl];
-          __stcs(reinterpret_cast<float4*>(a.y + ts.out_base + ((int64_t)(i - 1) << ts.m) + (e & ((1 << tl) - 1))), v);
-        };
-        fft_inplace<i - 1, NT, false>(Z, tn_log - i, a.tw, src, sink);
-        __syncthreads();
-      }
-    });
   }
 }
 
@@ -199,32 +211,39 @@ __global__ void k_fwd_tiny(const FwdArgs a) {
 
 // =================================================================== window
 
-// One window of level i (h = 2^(i-1) <= 2^13 points of odd-bin DFT) per item.
-template <int LB>
-__device__ __forceinline__ void window_level(const FwdArgs& a, const LevelItem& it, float2* Z) {
+// One window of level i (13 <= i <= 14: h = 2^(i-1) = 2^12 or 2^13 odd-bin
+// DFT points) per CTA: z from x, DFT_h in shared memory, even bins from the
+// level-(i-1) children in y, (even, odd) pairs stored at 2k.
+__global__ void __launch_bounds__(kWinThreads) k_fwd_window(const FwdArgs a) {
   constexpr int NT = kWinThreads;
-  constexpr int h = 1 << LB;
-  const int i = LB + 1;
+  extern __shared__ __align__(1024) float2 sm[];
+  float2* Z = sm;                               // 2^13 (pad8)
+  float2* TQ = sm + pad8_size(1 << kWinMaxLog); // quarter-wave w_{2^13}
+  if (blockIdx.x >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  const int i = a.level;
+  const int LB = i - 1;
+  const int64_t h = (int64_t)1 << LB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t ws = (int64_t)it.window << i;
   const int64_t xs = sd.in_off + ws;
   const float2* yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
-  auto src = [&](int, int n) -> float2 {
+  load_twq<NT>(TQ, kWinMaxLog, a.tw);
+  __syncthreads();
+  const TwQ tw{TQ, kWinMaxLog};
+  auto src = [&](int, int n) MRDFT_INL -> float2 {
     return cmul(csub(load_x1(a, xs + n), load_x1(a, xs + h + n)), tw_any(a.tw, i, n));
   };
-  auto sink = [&](int, int k, float2 odd) MRDFT_INL {
-    const float2 ev = cadd(__ldg(yprev + k), __ldg(yprev + h + k));
-    __stcs(reinterpret_cast<float4*>(ycur + 2 * k), make_float4(ev.x, ev.y, odd.x, odd.y));
+  const bool reread = sd.m > i;  // children of the next level: keep in L2
+  auto sink = [&](int, int, int k, float2 odd) MRDFT_INL {
+    const float2 ev = cadd(__ldcg(yprev + k), __ldcg(yprev + h + k));
+    const float4 v = make_float4(ev.x, ev.y, odd.x, odd.y);
+    float4* dst = reinterpret_cast<float4*>(ycur + 2 * k);
+    if (reread) __stcg(dst, v);
+    else __stcs(dst, v);
   };
-  fft_inplace<LB, NT, false>(Z, 0, a.tw, src, sink);
-}
-
-template <int LB>
-__global__ void __launch_bounds__(kWinThreads) k_fwd_window(const FwdArgs a) {
-  extern __shared__ __align__(1024) float2 sm[];
-  if (blockIdx.x >= a.nitems) return;
-  window_level<LB>(a, reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x], sm);
+  cg_fft<kTileLog, kWinMaxLog, NT, 32, false, false>(Z, LB, 0, tw, src, NoPre{}, sink);
 }
 
 // =============================================================== two-pass
@@ -233,120 +252,98 @@ __global__ void __launch_bounds__(kWinThreads) k_fwd_window(const FwdArgs a) {
 // cols: item (sig, window, block) covers chunk offsets r in [r0, r0 + RC),
 //   RC = 2^14 / Q.  z[r + C q] (q < Q) -> DFT_Q over q -> times w_h^(r k2)
 //   -> scratch G[window][k2][r].
-template <int QB>
-__device__ __forceinline__ void cols_level(const FwdArgs& a, const LevelItem& it, float2* S) {
+__global__ void __launch_bounds__(kPassThreads) k_fwd_cols(const FwdArgs a) {
   constexpr int NT = kPassThreads;
   constexpr int CB = kColsLog, C = 1 << CB;
-  constexpr int Q = 1 << QB;
-  constexpr int RCB = 14 - QB;  // log2 of columns per item
-  constexpr int RC = 1 << RCB;
-  constexpr int HB = QB + CB;   // log2 h
-  const int i = HB + 1;
+  extern __shared__ __align__(1024) float2 sm[];
+  float2* S = sm;                       // 2^14 (pad8), column r position q at q RC + r
+  float2* TQ = sm + pad8_size(kPassElems);  // quarter-wave w_{2^13}
+  if (blockIdx.x >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  const int i = a.level;
+  const int HB = i - 1, QB = HB - CB;
+  const int RCB = 14 - QB;
+  const int RC = 1 << RCB;
+  const int Q = 1 << QB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t ws = (int64_t)it.window << i;
   const int64_t xs = sd.in_off + ws;
   const int r0 = it.block << RCB;
-  constexpr int64_t h = (int64_t)1 << HB;
-  // load z[r0 + r + C q] into S[r][q]
+  const int64_t h = (int64_t)1 << HB;
+  load_twq<NT>(TQ, kWinMaxLog, a.tw);
   for (int e = threadIdx.x; e < RC * Q; e += NT) {
     const int r = e & (RC - 1), q = e >> RCB;
     const int64_t n = (int64_t)q * C + r0 + r;
     const float2 z = cmul(csub(load_x1(a, xs + n), load_x1(a, xs + h + n)), tw_any(a.tw, i, n));
-    S[swzf((r << QB) + q)] = z;
+    S[pad8(e)] = z;  // e = q RC + r
   }
   __syncthreads();
+  const TwQ tw{TQ, kWinMaxLog};
   float2* G = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((b << QB) + n)]; };
-  auto sink = [&](int b, int k2, float2 v) MRDFT_INL {
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[pad8((n << RCB) + b)]; };
+  auto sink = [&](int, int b, int k2, float2 v) MRDFT_INL {
     const int r = r0 + b;
     __stcg(G + ((int64_t)k2 << CB) + r, cmul(v, tw_any(a.tw, HB, (int64_t)r * k2)));
   };
-  if constexpr (QB >= 1) fft_inplace<QB, NT, true>(S, RCB, a.tw, src, sink);
-}
-
-template <int QB>
-__global__ void __launch_bounds__(kPassThreads) k_fwd_cols(const FwdArgs a) {
-  extern __shared__ __align__(1024) float2 sm[];
-  if (blockIdx.x >= a.nitems) return;
-  cols_level<QB>(a, reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x], sm);
+  cg_fft<2, kWinMaxLog, NT, 32, true, false>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
 // rows: item (sig, window, block) covers residues k2 in [k0, k0 + KC),
 //   KC = 2^14 / C = 4.  G[window][k2][0..C) -> DFT_C -> odd bin k = Q k1 + k2,
 //   even bin from the children; (even, odd) pairs stored at 2k.
-template <int QB>
-__device__ __forceinline__ void rows_level(const FwdArgs& a, const LevelItem& it, float2* S) {
+__global__ void __launch_bounds__(kPassThreads) k_fwd_rows(const FwdArgs a) {
   constexpr int NT = kPassThreads;
   constexpr int CB = kColsLog, C = 1 << CB;
   constexpr int KCB = 14 - CB, KC = 1 << KCB;
-  constexpr int HB = QB + CB;
-  constexpr int64_t h = (int64_t)1 << HB;
-  const int i = HB + 1;
+  extern __shared__ __align__(1024) float2 sm[];
+  float2* S = sm;                          // sequence j position r at r KC + j (pad8)
+  float2* TQ = sm + pad8_size(kPassElems);
+  if (blockIdx.x >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  const int i = a.level;
+  const int HB = i - 1, QB = HB - CB;
+  const int64_t h = (int64_t)1 << HB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t ws = (int64_t)it.window << i;
   const int k0 = it.block << KCB;
   const float2* G = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
+  load_twq<NT>(TQ, CB, a.tw);
+#pragma unroll 4
   for (int e = threadIdx.x; e < KC * C; e += NT) {
     const int r = e & (C - 1), j = e >> CB;
-    S[swzf((j << CB) + r)] = __ldcg(G + ((int64_t)(k0 + j) << CB) + r);
+    S[pad8((r << KCB) + j)] = __ldcg(G + ((int64_t)(k0 + j) << CB) + r);
   }
   __syncthreads();
+  // the intermediate rows are dead now: drop them from L2 without write-back
+  for (int l = threadIdx.x; l < KC * C / 16; l += NT) discard_l2(G + ((int64_t)k0 << CB) + 16 * l);
+  const TwQ tw{TQ, CB};
   const float2* yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((b << CB) + n)]; };
-  auto sink = [&](int b, int k1, float2 odd) MRDFT_INL {
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[pad8((n << KCB) + b)]; };
+  const bool reread = sd.m > i;
+  auto sink = [&](int, int b, int k1, float2 odd) MRDFT_INL {
     const int64_t k = ((int64_t)k1 << QB) + k0 + b;
-    const float2 ev = cadd(__ldg(yprev + k), __ldg(yprev + h + k));
-    __stcs(reinterpret_cast<float4*>(ycur + 2 * k), make_float4(ev.x, ev.y, odd.x, odd.y));
+    const float2 ev = cadd(__ldcg(yprev + k), __ldcg(yprev + h + k));
+    const float4 v = make_float4(ev.x, ev.y, odd.x, odd.y);
+    float4* dst = reinterpret_cast<float4*>(ycur + 2 * k);
+    if (reread) __stcg(dst, v);
+    else __stcs(dst, v);
   };
-  fft_inplace<CB, NT, true>(S, KCB, a.tw, src, sink);
-}
-
-template <int QB>
-__global__ void __launch_bounds__(kPassThreads) k_fwd_rows(const FwdArgs a) {
-  extern __shared__ __align__(1024) float2 sm[];
-  if (blockIdx.x >= a.nitems) return;
-  rows_level<QB>(a, reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x], sm);
+  cg_fft<CB, CB, NT, 32, true, false>(S, CB, KCB, tw, src, NoPre{}, sink);
 }
 
 // ================================================================ launchers
 
-static constexpr size_t kTileSmem = (size_t)(3 * kTile + kTile / 2) * sizeof(float2) + kMaxPack * sizeof(TileSig);
-static constexpr size_t kWinSmem = (size_t)(1 << kWinMaxLog) * sizeof(float2);
-static constexpr size_t kPassSmem = (size_t)kPassElems * sizeof(float2);
-
-// kernel tables indexed by level
-using FwdKernel = void (*)(const FwdArgs);
-static FwdKernel win_kernel(int level) {
-  switch (level) {
-    case 13: return k_fwd_window<12>;
-    case 14: return k_fwd_window<13>;
-    default: return nullptr;
-  }
-}
-template <int QB>
-static void pass_pair(int level, FwdKernel* c, FwdKernel* r) {
-  if constexpr (QB <= 13) {
-    if (level == QB + kColsLog + 1) {
-      *c = k_fwd_cols<QB>;
-      *r = k_fwd_rows<QB>;
-      return;
-    }
-    pass_pair<QB + 1>(level, c, r);
-  }
-}
+static constexpr size_t kTileSmem = (size_t)(2 * kTile + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kMaxPack * sizeof(TileSig);
+static constexpr size_t kWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog)) * sizeof(float2);
+static constexpr size_t kPassSmem = (size_t)(pad8_size(kPassElems) + twq_size(kWinMaxLog)) * sizeof(float2);
 
 cudaError_t set_fwd_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_fwd_tile<kTileLog, kTileThreads>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-  for (int lv = 13; lv <= 14 && e == cudaSuccess; ++lv)
-    e = cudaFuncSetAttribute(win_kernel(lv), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmem);
-  for (int lv = 15; lv <= 26 && e == cudaSuccess; ++lv) {
-    FwdKernel c = nullptr, r = nullptr;
-    pass_pair<2>(lv, &c, &r);
-    e = cudaFuncSetAttribute(c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(r, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
-  }
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
   return e;
 }
 
@@ -359,23 +356,15 @@ cudaError_t launch_fwd_tiny(const FwdArgs& a, int nsig_tiny, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_window(const FwdArgs& a, int grid, cudaStream_t s) {
-  FwdKernel k = win_kernel(a.level);
-  if (!k) return cudaErrorInvalidValue;
-  k<<<grid, kWinThreads, kWinSmem, s>>>(a);
+  k_fwd_window<<<grid, kWinThreads, kWinSmem, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s) {
-  FwdKernel c = nullptr, r = nullptr;
-  pass_pair<2>(a.level, &c, &r);
-  if (!c) return cudaErrorInvalidValue;
-  c<<<grid, kPassThreads, kPassSmem, s>>>(a);
+  k_fwd_cols<<<grid, kPassThreads, kPassSmem, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_rows(const FwdArgs& a, int grid, cudaStream_t s) {
-  FwdKernel c = nullptr, r = nullptr;
-  pass_pair<2>(a.level, &c, &r);
-  if (!r) return cudaErrorInvalidValue;
-  r<<<grid, kPassThreads, kPassSmem, s>>>(a);
+  k_fwd_rows<<<grid, kPassThreads, kPassSmem, s>>>(a);
   return cudaGetLastError();
 }
 

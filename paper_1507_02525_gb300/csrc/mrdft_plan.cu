@@ -10,6 +10,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -32,11 +33,23 @@ namespace {
 
 constexpr int kMaxLog = 26;
 
-struct LevelLaunch {
-  int level;
-  int kind;       // 0 window, 1 two-pass (cols + rows)
-  int64_t off;    // first item in the level item array
-  int count;      // items of the window kernel, or of each pass
+// One kernel launch (or, for two-pass levels, the cols + rows pair) over a
+// contiguous range of a device work list.
+enum LaunchKind { LK_TILE = 0, LK_WIN = 1, LK_PASS = 2 };
+struct Launch {
+  int kind;
+  int level;      // level built (window / two-pass)
+  int64_t off;    // first item in d_tiles or d_levels
+  int count;      // items (per pass for two-pass levels)
+  int64_t bytes;  // algorithmic bytes: input read once + outputs written
+};
+
+// A segment: a group of signals or a window of one signal, at most 2^seg_log
+// samples, whose levels up to seg_log run as one chain of launches on one
+// stream -- small enough that x, the children spectra and the two-pass
+// intermediate stay in L2 between the launches of the chain.
+struct Segment {
+  std::vector<Launch> chain;  // tile launch first, then levels ascending
 };
 
 struct GraphKey {
@@ -73,7 +86,13 @@ struct mrdft_plan_s {
   int32_t* d_tiny_ids = nullptr;
   int n_tiny = 0;
   LevelItem* d_levels = nullptr;
-  std::vector<LevelLaunch> level_launches;  // ascending level
+  std::vector<Segment> segments;
+  std::vector<Launch> top;  // levels above seg_log, ascending, whole plan
+  int seg_log = 20;
+  int nstreams = 4;
+  std::vector<cudaStream_t> workers;
+  std::vector<cudaEvent_t> ev_join;
+  cudaEvent_t ev_fork = nullptr;
   float2* d_tw13 = nullptr;
   float2* d_twlo = nullptr;
   float2* d_twhi = nullptr;
@@ -88,6 +107,19 @@ struct mrdft_plan_s {
 
   std::map<GraphKey, cudaGraphExec_t> fwd_graphs, adj_graphs;
   std::string err = "no error";
+
+  // optional per-kernel timing (events around every launch, no graph replay)
+  bool timing = false;
+  struct Pending {
+    int kind;
+    cudaEvent_t a, b;
+    int64_t bytes;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> event_pool;
+  double t_ms[MRDFT_KIND_COUNT] = {0};
+  int64_t t_launches[MRDFT_KIND_COUNT] = {0};
+  int64_t t_bytes[MRDFT_KIND_COUNT] = {0};
 };
 
 namespace {
@@ -127,7 +159,53 @@ float2 root32(int64_t e, int64_t L) {
   return make_float2((float)std::cos(a), (float)std::sin(a));
 }
 
+cudaEvent_t pool_event(mrdft_plan_s* p) {
+  if (!p->event_pool.empty()) {
+    cudaEvent_t e = p->event_pool.back();
+    p->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch `fn` bracketed by timing events when the plan's timing is on.
+template <class F>
+cudaError_t timed(mrdft_plan_s* p, int kind, int64_t bytes, cudaStream_t st, F&& fn) {
+  if (!p->timing) return fn();
+  mrdft_plan_s::Pending pd{kind, pool_event(p), pool_event(p), bytes};
+  cudaEventRecord(pd.a, st);
+  cudaError_t e = fn();
+  cudaEventRecord(pd.b, st);
+  p->pending.push_back(pd);
+  return e;
+}
+
+void collect_timing(mrdft_plan_s* p) {
+  for (auto& pd : p->pending) {
+    cudaEventSynchronize(pd.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, pd.a, pd.b);
+    p->t_ms[pd.kind] += ms;
+    p->t_launches[pd.kind] += 1;
+    p->t_bytes[pd.kind] += pd.bytes;
+    p->event_pool.push_back(pd.a);
+    p->event_pool.push_back(pd.b);
+  }
+  p->pending.clear();
+}
+
 void release(mrdft_plan_s* p) {
+  collect_timing(p);
+  for (cudaStream_t w : p->workers) cudaStreamDestroy(w);
+  p->workers.clear();
+  for (cudaEvent_t e : p->ev_join) cudaEventDestroy(e);
+  p->ev_join.clear();
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  p->ev_fork = nullptr;
+  for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
+  p->event_pool.clear();
   for (auto& kv : p->fwd_graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : p->adj_graphs) cudaGraphExecDestroy(kv.second);
   p->fwd_graphs.clear();
@@ -178,71 +256,133 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
   p->out_elems = out_off;
   p->half_elems = aux_off;
 
-  // ---- tile work list: signals grouped by m, small ones packed per tile
+  // ---- segments: units of <= 2^S samples (whole signals, or windows of 2^S
+  // of longer signals), signals ordered by length (longest first)
+  {
+    const char* env = getenv("MRDFT_SEG_LOG");
+    if (env) p->seg_log = std::max(kTileLog, std::min(kMaxLog, atoi(env)));
+    env = getenv("MRDFT_STREAMS");
+    if (env) p->nstreams = std::max(1, std::min(16, atoi(env)));
+  }
+  const int S = p->seg_log;
+  const int64_t in_b = p->dtype == MRDFT_R32 ? 4 : 8;
   std::vector<int32_t> order(batch);
   for (int64_t s = 0; s < batch; ++s) order[s] = (int32_t)s;
   std::stable_sort(order.begin(), order.end(),
                    [&](int32_t a, int32_t b) { return p->sigs[a].m > p->sigs[b].m; });
-  std::vector<int32_t> tile_ids, tiny_ids;
+  struct Unit {
+    int32_t sig;
+    int32_t w;  // window index at level U
+    int U;      // min(m, S)
+  };
+  std::vector<std::vector<Unit>> seg_units;
+  std::vector<int32_t> tiny_ids;
+  {
+    std::vector<Unit> cur;
+    int64_t cur_n = 0;
+    for (int32_t s : order) {
+      const int m = p->sigs[s].m;
+      if (m <= 4) {
+        tiny_ids.push_back(s);
+        continue;
+      }
+      const int U = std::min(m, S);
+      const int64_t nu = int64_t(1) << (m - U);
+      for (int64_t w = 0; w < nu; ++w) {
+        if (cur_n + (int64_t(1) << U) > (int64_t(1) << S) && !cur.empty()) {
+          seg_units.push_back(cur);
+          cur.clear();
+          cur_n = 0;
+        }
+        cur.push_back(Unit{s, (int32_t)w, U});
+        cur_n += int64_t(1) << U;
+      }
+    }
+    if (!cur.empty()) seg_units.push_back(cur);
+  }
+  std::vector<int32_t> tile_ids;
   std::vector<TileItem> tiles;
-  size_t q = 0;
-  while (q < order.size()) {
-    const int m = p->sigs[order[q]].m;
-    if (m <= 4) {
-      tiny_ids.push_back(order[q]);
-      ++q;
-      continue;
-    }
-    if (m >= kTileLog) {
+  std::vector<LevelItem> litems;
+  auto pass_blocks = [](int i) { return std::max(1, (1 << (i - 1 - kColsLog)) / 4); };
+  auto add_level_items = [&](int i, int32_t sig, int64_t w0, int64_t nw, Launch& L) {
+    const int nblk = i <= kWinMaxLog + 1 ? 1 : pass_blocks(i);
+    for (int64_t w = w0; w < w0 + nw; ++w)
+      for (int b = 0; b < nblk; ++b) litems.push_back(LevelItem{sig, (int32_t)w, b, 0});
+    L.bytes += 8 * nw * (int64_t(1) << i);
+  };
+  for (const auto& units : seg_units) {
+    Segment seg;
+    // tile launch
+    Launch T{};
+    T.kind = LK_TILE;
+    T.off = (int64_t)tiles.size();
+    size_t q = 0;
+    while (q < units.size()) {
+      const Unit& u = units[q];
+      const int m = p->sigs[u.sig].m;
+      if (m >= kTileLog) {
+        const int32_t list = (int32_t)tile_ids.size();
+        tile_ids.push_back(u.sig);
+        const int64_t per = int64_t(1) << (u.U - kTileLog);
+        for (int64_t t = u.w * per; t < (u.w + 1) * per; ++t)
+          tiles.push_back(TileItem{list, 1, (int16_t)kTileLog, (int32_t)t, 0});
+        T.bytes += (int64_t(1) << u.U) * (in_b + 8 * kTileLog);
+        ++q;
+        continue;
+      }
+      // pack whole signals of equal length into one tile; the pack size is a
+      // power of two (the in-tile FFT works on 2^k windows)
+      const int per = 1 << (kTileLog - m);
+      size_t avail = 0;
+      while (q + avail < units.size() && p->sigs[units[q + avail].sig].m == m && (int)avail < per) ++avail;
+      int n = 1;
+      while ((size_t)(n * 2) <= avail) n *= 2;
       const int32_t list = (int32_t)tile_ids.size();
-      tile_ids.push_back(order[q]);
-      const int64_t ntile = int64_t(1) << (m - kTileLog);
-      for (int64_t t = 0; t < ntile; ++t) tiles.push_back(TileItem{list, 1, (int16_t)kTileLog, (int32_t)t, 0});
-      ++q;
-      continue;
+      for (int k = 0; k < n; ++k) tile_ids.push_back(units[q + k].sig);
+      q += n;
+      tiles.push_back(TileItem{list, (int16_t)n, (int16_t)m, 0, 0});
+      T.bytes += ((int64_t)n << m) * (in_b + 8 * m);
     }
-    // pack whole signals of equal length into one tile; the pack size is a
-    // power of two (the in-tile FFT works on 2^k windows)
-    const int per = 1 << (kTileLog - m);
-    size_t avail = 0;
-    while (q + avail < order.size() && p->sigs[order[q + avail]].m == m && (int)avail < per) ++avail;
-    int n = 1;
-    while ((size_t)(n * 2) <= avail) n *= 2;
-    const int32_t list = (int32_t)tile_ids.size();
-    for (int k = 0; k < n; ++k) tile_ids.push_back(order[q + k]);
-    q += n;
-    tiles.push_back(TileItem{list, (int16_t)n, (int16_t)m, 0, 0});
+    T.count = (int)((int64_t)tiles.size() - T.off);
+    if (T.count) seg.chain.push_back(T);
+    // levels above the tile, inside the segment
+    for (int i = kTileLog + 1; i <= S; ++i) {
+      Launch L{};
+      L.kind = i <= kWinMaxLog + 1 ? LK_WIN : LK_PASS;
+      L.level = i;
+      L.off = (int64_t)litems.size();
+      for (const Unit& u : units)
+        if (u.U >= i) add_level_items(i, u.sig, (int64_t)u.w << (u.U - i), int64_t(1) << (u.U - i), L);
+      L.count = (int)((int64_t)litems.size() - L.off);
+      if (L.count) seg.chain.push_back(L);
+    }
+    p->segments.push_back(seg);
+  }
+  // levels above the segments, over whole signals
+  for (int i = S + 1; i <= p->max_m; ++i) {
+    Launch L{};
+    L.kind = i <= kWinMaxLog + 1 ? LK_WIN : LK_PASS;
+    L.level = i;
+    L.off = (int64_t)litems.size();
+    for (int32_t s : order)
+      if (p->sigs[s].m >= i) add_level_items(i, s, 0, int64_t(1) << (p->sigs[s].m - i), L);
+    L.count = (int)((int64_t)litems.size() - L.off);
+    if (L.count) p->top.push_back(L);
   }
   p->n_tiles = (int)tiles.size();
   p->n_tiny = (int)tiny_ids.size();
 
-  // ---- level work lists (levels above the tile)
-  std::vector<LevelItem> litems;
-  for (int i = kTileLog + 1; i <= p->max_m; ++i) {
-    LevelLaunch L{};
-    L.level = i;
-    L.off = (int64_t)litems.size();
-    if (i <= kWinMaxLog + 1) {
-      L.kind = 0;
-      for (int64_t s = 0; s < batch; ++s) {
-        if (p->sigs[s].m < i) continue;
-        const int64_t nw = int64_t(1) << (p->sigs[s].m - i);
-        for (int64_t w = 0; w < nw; ++w) litems.push_back(LevelItem{(int32_t)s, (int32_t)w, 0, 0});
-      }
-    } else {
-      L.kind = 1;
-      const int QB = i - 1 - kColsLog;
-      const int nblk = std::max(1, (1 << QB) / 4);  // cols: C / RC ; rows: Q / KC
-      for (int64_t s = 0; s < batch; ++s) {
-        if (p->sigs[s].m < i) continue;
-        const int64_t nw = int64_t(1) << (p->sigs[s].m - i);
-        for (int64_t w = 0; w < nw; ++w)
-          for (int b = 0; b < nblk; ++b) litems.push_back(LevelItem{(int32_t)s, (int32_t)w, b, 0});
-      }
-    }
-    L.count = (int)((int64_t)litems.size() - L.off);
-    p->level_launches.push_back(L);
+  // streams and events for the concurrent segment chains
+  const int nw = std::min<int>(p->nstreams, (int)p->segments.size());
+  for (int k = 0; k < std::max(0, nw); ++k) {
+    cudaStream_t w = nullptr;
+    cudaEvent_t e = nullptr;
+    MRDFT_CUDA(p, cudaStreamCreateWithFlags(&w, cudaStreamNonBlocking));
+    p->workers.push_back(w);
+    MRDFT_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    p->ev_join.push_back(e);
   }
+  MRDFT_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
 
   // ---- twiddles: FP64 on the host, rounded once
   std::vector<float2> tw13(1 << kTwLog), twlo(1 << kTwSplit), twhi(1 << (kTwBigLog - kTwSplit));
@@ -276,6 +416,49 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
 
 Twiddles twiddles(const mrdft_plan_s* p) { return Twiddles{p->d_tw13, p->d_twlo, p->d_twhi}; }
 
+mrdft_status launch_fwd(mrdft_plan_s* p, FwdArgs a, const Launch& L, cudaStream_t st) {
+  a.level = L.level;
+  a.nitems = L.count;
+  if (L.kind == LK_TILE) {
+    a.sig_ids = p->d_tile_ids;
+    a.items = p->d_tiles + L.off;
+    MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_TILE, L.bytes, st, [&] { return launch_fwd_tile(a, L.count, st); }));
+  } else if (L.kind == LK_WIN) {
+    a.items = p->d_levels + L.off;
+    MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_WINDOW, L.bytes, st, [&] { return launch_fwd_window(a, L.count, st); }));
+  } else {
+    a.items = p->d_levels + L.off;
+    MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_COLS, 0, st, [&] { return launch_fwd_cols(a, L.count, st); }));
+    MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_ROWS, L.bytes, st, [&] { return launch_fwd_rows(a, L.count, st); }));
+  }
+  return MRDFT_OK;
+}
+
+// Fork the segment chains over the worker streams (event fork / join on the
+// caller's stream, which also works under stream capture).
+template <class F>
+mrdft_status run_segments(mrdft_plan_s* p, cudaStream_t st, F&& chain) {
+  const int nw = (int)p->workers.size();
+  if (nw <= 1) {
+    for (size_t j = 0; j < p->segments.size(); ++j) {
+      mrdft_status r = chain(p->segments[j], st);
+      if (r != MRDFT_OK) return r;
+    }
+    return MRDFT_OK;
+  }
+  MRDFT_CUDA(p, cudaEventRecord(p->ev_fork, st));
+  for (int k = 0; k < nw; ++k) MRDFT_CUDA(p, cudaStreamWaitEvent(p->workers[k], p->ev_fork, 0));
+  for (size_t j = 0; j < p->segments.size(); ++j) {
+    mrdft_status r = chain(p->segments[j], p->workers[j % nw]);
+    if (r != MRDFT_OK) return r;
+  }
+  for (int k = 0; k < nw; ++k) {
+    MRDFT_CUDA(p, cudaEventRecord(p->ev_join[k], p->workers[k]));
+    MRDFT_CUDA(p, cudaStreamWaitEvent(st, p->ev_join[k], 0));
+  }
+  return MRDFT_OK;
+}
+
 mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream_t st) {
   FwdArgs a{};
   a.x = x;
@@ -285,28 +468,45 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
   a.scratch = p->d_scratch;
   a.tw = twiddles(p);
   a.status = p->d_status;
-  if (p->n_tiles) {
-    a.sig_ids = p->d_tile_ids;
-    a.items = p->d_tiles;
-    a.nitems = p->n_tiles;
-    MRDFT_CUDA(p, launch_fwd_tile(a, p->n_tiles, st));
-  }
   if (p->n_tiny) {
-    a.sig_ids = p->d_tiny_ids;
-    a.items = nullptr;
-    a.nitems = p->n_tiny;
-    MRDFT_CUDA(p, launch_fwd_tiny(a, p->n_tiny, st));
+    FwdArgs t = a;
+    t.sig_ids = p->d_tiny_ids;
+    t.nitems = p->n_tiny;
+    MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_TINY, 0, st, [&] { return launch_fwd_tiny(t, p->n_tiny, st); }));
   }
-  for (const LevelLaunch& L : p->level_launches) {
-    a.level = L.level;
-    a.items = p->d_levels + L.off;
-    a.nitems = L.count;
-    if (L.kind == 0) {
-      MRDFT_CUDA(p, launch_fwd_window(a, L.count, st));
-    } else {
-      MRDFT_CUDA(p, launch_fwd_cols(a, L.count, st));
-      MRDFT_CUDA(p, launch_fwd_rows(a, L.count, st));
+  mrdft_status r = run_segments(p, st, [&](const Segment& seg, cudaStream_t s) {
+    for (const Launch& L : seg.chain) {
+      mrdft_status q = launch_fwd(p, a, L, s);
+      if (q != MRDFT_OK) return q;
     }
+    return MRDFT_OK;
+  });
+  if (r != MRDFT_OK) return r;
+  for (const Launch& L : p->top) {
+    r = launch_fwd(p, a, L, st);
+    if (r != MRDFT_OK) return r;
+  }
+  return MRDFT_OK;
+}
+
+mrdft_status launch_adj(mrdft_plan_s* p, AdjArgs a, const Launch& L, cudaStream_t st) {
+  a.level = L.level;
+  a.nitems = L.count;
+  if (L.kind == LK_TILE) {
+    a.sig_ids = p->d_tile_ids;
+    a.items = p->d_tiles + L.off;
+    a.e_in = ((kTileLog + 1) & 1) ? p->d_e1 : p->d_e0;
+    MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_TILE, L.bytes, st, [&] { return launch_adj_tile(a, L.count, st); }));
+    return MRDFT_OK;
+  }
+  a.items = p->d_levels + L.off;
+  a.e_out = (L.level & 1) ? p->d_e1 : p->d_e0;
+  a.e_in = ((L.level + 1) & 1) ? p->d_e1 : p->d_e0;
+  if (L.kind == LK_WIN) {
+    MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_WINDOW, L.bytes, st, [&] { return launch_adj_window(a, L.count, st); }));
+  } else {
+    MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_ROWS, L.bytes, st, [&] { return launch_adj_rows(a, L.count, st); }));
+    MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_COLS, 0, st, [&] { return launch_adj_cols(a, L.count, st); }));
   }
   return MRDFT_OK;
 }
@@ -320,32 +520,23 @@ mrdft_status enqueue_adjoint(mrdft_plan_s* p, const void* gy, void* gx, cudaStre
   a.scratch = p->d_scratch;
   a.tw = twiddles(p);
   a.status = p->d_status;
-  for (auto it = p->level_launches.rbegin(); it != p->level_launches.rend(); ++it) {
-    const LevelLaunch& L = *it;
-    a.level = L.level;
-    a.items = p->d_levels + L.off;
-    a.nitems = L.count;
-    a.e_out = (L.level & 1) ? p->d_e1 : p->d_e0;
-    a.e_in = ((L.level + 1) & 1) ? p->d_e1 : p->d_e0;
-    if (L.kind == 0) {
-      MRDFT_CUDA(p, launch_adj_window(a, L.count, st));
-    } else {
-      MRDFT_CUDA(p, launch_adj_rows(a, L.count, st));
-      MRDFT_CUDA(p, launch_adj_cols(a, L.count, st));
+  for (auto it = p->top.rbegin(); it != p->top.rend(); ++it) {
+    mrdft_status r = launch_adj(p, a, *it, st);
+    if (r != MRDFT_OK) return r;
+  }
+  mrdft_status r = run_segments(p, st, [&](const Segment& seg, cudaStream_t s) {
+    for (auto it = seg.chain.rbegin(); it != seg.chain.rend(); ++it) {
+      mrdft_status q = launch_adj(p, a, *it, s);
+      if (q != MRDFT_OK) return q;
     }
-  }
-  if (p->n_tiles) {
-    a.sig_ids = p->d_tile_ids;
-    a.items = p->d_tiles;
-    a.nitems = p->n_tiles;
-    a.e_in = ((kTileLog + 1) & 1) ? p->d_e1 : p->d_e0;
-    MRDFT_CUDA(p, launch_adj_tile(a, p->n_tiles, st));
-  }
+    return MRDFT_OK;
+  });
+  if (r != MRDFT_OK) return r;
   if (p->n_tiny) {
-    a.sig_ids = p->d_tiny_ids;
-    a.items = nullptr;
-    a.nitems = p->n_tiny;
-    MRDFT_CUDA(p, launch_adj_tiny(a, p->n_tiny, st));
+    AdjArgs t = a;
+    t.sig_ids = p->d_tiny_ids;
+    t.nitems = p->n_tiny;
+    MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_TINY, 0, st, [&] { return launch_adj_tiny(t, p->n_tiny, st); }));
   }
   return MRDFT_OK;
 }
@@ -357,7 +548,7 @@ mrdft_status run(mrdft_plan_s* p, std::map<GraphKey, cudaGraphExec_t>& cache, En
   int dev = -1;
   MRDFT_CUDA(p, cudaGetDevice(&dev));
   if (dev != p->device) return fail(p, MRDFT_EINVAL, "plan used on a different device than it was created on");
-  if (!(p->flags & MRDFT_FLAG_GRAPH)) return fn(p, in, out, st);
+  if (!(p->flags & MRDFT_FLAG_GRAPH) || p->timing) return fn(p, in, out, st);
   const GraphKey key{in, out, st};
   auto found = cache.find(key);
   if (found == cache.end()) {
@@ -494,11 +685,35 @@ const char* mrdft_last_error(mrdft_plan_t p) {
 
 mrdft_status mrdft_plan_info(mrdft_plan_t p, int32_t* tile_log, int32_t* fwd_launches, int32_t* adj_launches) {
   if (!p) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_info: plan is NULL");
-  int n = (p->n_tiles ? 1 : 0) + (p->n_tiny ? 1 : 0);
-  for (const LevelLaunch& L : p->level_launches) n += L.kind == 0 ? 1 : 2;
+  int n = p->n_tiny ? 1 : 0;
+  for (const Segment& g : p->segments)
+    for (const Launch& L : g.chain) n += L.kind == LK_PASS ? 2 : 1;
+  for (const Launch& L : p->top) n += L.kind == LK_PASS ? 2 : 1;
   if (tile_log) *tile_log = kTileLog;
   if (fwd_launches) *fwd_launches = n;
   if (adj_launches) *adj_launches = n;
+  return MRDFT_OK;
+}
+
+mrdft_status mrdft_timing_enable(mrdft_plan_t p, int enable) {
+  if (!p) return fail(nullptr, MRDFT_EINVAL, "mrdft_timing_enable: plan is NULL");
+  collect_timing(p);
+  p->timing = enable != 0;
+  for (int k = 0; k < MRDFT_KIND_COUNT; ++k) {
+    p->t_ms[k] = 0.0;
+    p->t_launches[k] = 0;
+    p->t_bytes[k] = 0;
+  }
+  return MRDFT_OK;
+}
+
+mrdft_status mrdft_timing_read(mrdft_plan_t p, int kind, double* ms, int64_t* launches, int64_t* bytes) {
+  if (!p) return fail(nullptr, MRDFT_EINVAL, "mrdft_timing_read: plan is NULL");
+  if (kind < 0 || kind >= MRDFT_KIND_COUNT) return fail(p, MRDFT_EINVAL, "mrdft_timing_read: bad kind");
+  collect_timing(p);
+  if (ms) *ms = p->t_ms[kind];
+  if (launches) *launches = p->t_launches[kind];
+  if (bytes) *bytes = p->t_bytes[kind];
   return MRDFT_OK;
 }
 
