@@ -87,7 +87,7 @@ __device__ __forceinline__ void adj_chunk_levels_4_1(const AdjArgs& a, const Adj
 }
 
 template <int TLOG, int NT>
-__global__ void __launch_bounds__(NT, 2) k_adj_tile(const AdjArgs a) {
+__global__ void __launch_bounds__(NT, 1) k_adj_tile(const AdjArgs a) {
   constexpr int T = 1 << TLOG;
   static_assert(T == 16 * NT, "tile = 16 samples per thread");
   extern __shared__ __align__(1024) float2 sm[];
@@ -147,10 +147,10 @@ __global__ void __launch_bounds__(NT, 2) k_adj_tile(const AdjArgs a) {
         p = make_float4(pe.x, pe.y, po.x, po.y);
       }
       Eout[swzf(w * h + (k >> 1))] = make_float2(g.x + p.x, g.y + p.y);
-      Z[pad8(w * h + (k >> 1))] = make_float2(g.z + p.z, -(g.w + p.w));
+      Z[swzf(w * h + (k >> 1))] = make_float2(g.z + p.z, -(g.w + p.w));
     }
     __syncthreads();
-    auto src = [&](int b, int n) MRDFT_INL -> float2 { return Z[pad8((b << (i - 1)) + n)]; };
+    auto src = [&](int b, int n) MRDFT_INL -> float2 { return Z[swzf((b << (i - 1)) + n)]; };
     auto sink = [&](int, int b, int n, float2 v) MRDFT_INL {
       const float2 c = cmulc(conjf2(v), twq_l(tw, i, n));  // conj(w^n) zb[n]
       const int base = b << i;
@@ -224,7 +224,7 @@ __device__ __forceinline__ void acc_add(const AdjArgs& a, const SigDesc& sd, int
   __stcg(p, c);
 }
 
-__global__ void __launch_bounds__(kWinThreads) k_adj_window(const AdjArgs a) {
+__global__ void __launch_bounds__(kWinThreads, 1) k_adj_window(const AdjArgs a) {
   constexpr int NT = kWinThreads;
   extern __shared__ __align__(1024) float2 sm[];
   float2* Z = sm;                               // pad8
@@ -240,18 +240,18 @@ __global__ void __launch_bounds__(kWinThreads) k_adj_window(const AdjArgs a) {
   for (int k = threadIdx.x; k < h; k += NT) {
     const float4 g = adj_G(a, sd, i, w, 2 * (int64_t)k);
     __stcg(a.e_out + sd.aux_off + (w << LB) + k, make_float2(g.x, g.y));
-    Z[pad8(k)] = make_float2(g.z, -g.w);
+    Z[swzf(k)] = make_float2(g.z, -g.w);
   }
   __syncthreads();
   const TwQ tw{TQ, kWinMaxLog};
   const int64_t ws = w << i;
-  auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[pad8(n)]; };
+  auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[swzf(n)]; };
   auto sink = [&](int, int, int n, float2 v) MRDFT_INL {
     const float2 c = cmulc(conjf2(v), tw_any(a.tw, i, n));
     acc_add(a, sd, i, ws + n, c);
     acc_add(a, sd, i, ws + h + n, make_float2(-c.x, -c.y));
   };
-  cg_fft<kTileLog, kWinMaxLog, NT, 32, false, false>(Z, LB, 0, tw, src, NoPre{}, sink);
+  cg_fft<kTileLog, kWinMaxLog, NT, (1 << kWinMaxLog) / NT, false, false>(Z, LB, 0, tw, src, NoPre{}, sink);
 }
 
 // =============================================================== two-pass
@@ -280,17 +280,17 @@ __global__ void __launch_bounds__(kPassThreads) k_adj_rows(const AdjArgs a) {
     const int64_t k = ((int64_t)k1 << QB) + k0 + j;
     const float4 g = adj_G(a, sd, i, w, 2 * k);
     __stcg(a.e_out + sd.aux_off + (w << HB) + k, make_float2(g.x, g.y));
-    S[pad8((j << CB) + k1)] = make_float2(g.z, -g.w);
+    S[swzf((j << CB) + k1)] = make_float2(g.z, -g.w);
   }
   __syncthreads();
   const TwQ tw{TQ, CB};
   float2* U = a.scratch + sd.aux_off + (w << HB);
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[pad8((b << CB) + n)]; };
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((b << CB) + n)]; };
   auto sink = [&](int, int b, int r, float2 v) MRDFT_INL {
     const int k2 = k0 + b;
     __stcg(U + ((int64_t)k2 << CB) + r, cmulc(conjf2(v), tw_any(a.tw, HB, (int64_t)r * k2)));
   };
-  cg_fft<CB, CB, NT, 32, false, false>(S, CB, KCB, tw, src, NoPre{}, sink);
+  cg_fft<CB, CB, NT, kPassElems / NT, false, false>(S, CB, KCB, tw, src, NoPre{}, sink);
 }
 
 // cols: item (sig, window, block) covers chunk offsets r in [r0, r0 + RC):
@@ -317,7 +317,7 @@ __global__ void __launch_bounds__(kPassThreads) k_adj_cols(const AdjArgs a) {
 #pragma unroll 4
   for (int e = threadIdx.x; e < RC * Q; e += NT) {
     const int r = e & (RC - 1), k2 = e >> RCB;
-    S[pad8(e)] = conjf2(__ldcg(U + ((int64_t)k2 << CB) + r0 + r));  // e = k2 RC + r
+    S[swzf(e)] = conjf2(__ldcg(U + ((int64_t)k2 << CB) + r0 + r));  // e = k2 RC + r
   }
   __syncthreads();
   // this block's columns of the intermediate are dead: drop them from L2
@@ -326,14 +326,14 @@ __global__ void __launch_bounds__(kPassThreads) k_adj_cols(const AdjArgs a) {
       discard_l2(U + ((int64_t)(l / (RC / 16)) << CB) + r0 + 16 * (l % (RC / 16)));
   const TwQ tw{TQ, kWinMaxLog};
   const int64_t ws = w << i;
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[pad8((n << RCB) + b)]; };
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((n << RCB) + b)]; };
   auto sink = [&](int, int b, int q, float2 v) MRDFT_INL {
     const int64_t n = ((int64_t)q << CB) + r0 + b;
     const float2 c = cmulc(conjf2(v), tw_any(a.tw, i, n));
     acc_add(a, sd, i, ws + n, c);
     acc_add(a, sd, i, ws + h + n, make_float2(-c.x, -c.y));
   };
-  cg_fft<2, kWinMaxLog, NT, 32, true, false>(S, QB, RCB, tw, src, NoPre{}, sink);
+  cg_fft<2, kWinMaxLog, NT, kPassElems / NT, true, false>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
 // ================================================================ launchers

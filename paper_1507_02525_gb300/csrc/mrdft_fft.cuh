@@ -11,7 +11,11 @@
 //
 // Shared layout: element a of the work buffer lives at pad8(a) = a + a/8, so
 // both the 8-consecutive reads and the lane-consecutive strided writes are
-// free of bank conflicts and their addresses are a base plus constants.
+// free of bank conflicts and their addresses are a base plus constants.  The
+// first pass reads its input through src(); callers that stage the input in
+// shared memory use the XOR layout swzf() there, which absorbs the
+// digit-reversed (power-of-two strided) read pattern; the first pass then
+// rewrites the buffer in place in the pad8 layout.
 // Sequences are stored sequence-major (b * L + pos) or, SEQ_MINOR,
 // position-major (pos * nseq + b, consecutive lanes on consecutive sequences).
 #pragma once
@@ -21,6 +25,10 @@ namespace mrdft {
 
 __device__ __forceinline__ int pad8(int a) { return a + (a >> 3); }
 __host__ __device__ constexpr int pad8_size(int n) { return n + n / 8; }
+// one pad element per 16 (level buffers: lane-consecutive and window-strided
+// 8-byte accesses stay conflict-free, and (2k, 2k+1) stay adjacent)
+__device__ __forceinline__ int pad16(int a) { return a + (a >> 4); }
+__host__ __device__ constexpr int pad16_size(int n) { return n + n / 16; }
 
 // Twiddles w_{2^TB}^e from a quarter-wave table q[r] = w_{2^TB}^r, r < 2^(TB-2)
 // (FP64 values rounded once), using w^(r + s 2^(TB-2)) = (-j)^s w^r.  The

@@ -105,18 +105,17 @@ __device__ __forceinline__ void tile_chunk_levels_1_4(const FwdArgs& a, const fl
       __stcs(dst + q, make_float4(yr[2 * q].x, yr[2 * q].y, yr[2 * q + 1].x, yr[2 * q + 1].y));
   });
 #pragma unroll
-  for (int q = 0; q < 8; ++q)
-    st4s(B4 + swz128((chunk << 4) + 2 * q), make_float4(yr[2 * q].x, yr[2 * q].y, yr[2 * q + 1].x, yr[2 * q + 1].y));
+  for (int q = 0; q < 16; ++q) B4[pad16((chunk << 4) + q)] = yr[q];
 }
 
 template <int TLOG, int NT>
-__global__ void __launch_bounds__(NT, 2) k_fwd_tile(const FwdArgs a) {
+__global__ void __launch_bounds__(NT, 1) k_fwd_tile(const FwdArgs a) {
   constexpr int T = 1 << TLOG;
   static_assert(T == 16 * NT, "tile = 16 samples per thread");
   extern __shared__ __align__(1024) float2 sm[];
   float2* X = sm;                       // x tile (swz128)
-  float2* B = sm + T;                   // current level, updated in place (swz128)
-  float2* Z = sm + 2 * T;               // odd-bin DFT work area (pad8)
+  float2* B = sm + T;                   // current level, updated in place (pad16)
+  float2* Z = B + pad16_size(T);        // odd-bin DFT work area (pad8)
   float2* TQ = Z + pad8_size(T / 2);    // quarter-wave w_{2^TLOG} (padded)
   TileSig* TS = reinterpret_cast<TileSig*>(TQ + twq_size(TLOG));
   const int tid = threadIdx.x;
@@ -162,10 +161,13 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_tile(const FwdArgs a) {
   // ---- levels 5..tlog through the shared-memory FFT engine; B is updated in
   // place: every child read (pre) happens before the barrier in the last pass
   const TwQ tw{TQ, TLOG};
+  const bool single = it.nsig == 1;
 #pragma unroll 1
   for (int i = 5; i <= tl; ++i) {
     const int h = 1 << (i - 1);
     const bool keep = i < tl;  // the next level reads this one
+    float2* ylev = a.y + TS[0].out_base + ((int64_t)(i - 1) << TS[0].m);  // single-signal tile
+    const bool l2keep = i == tl && TS[0].m > tl;  // re-read as children of level tl+1
     float2 ev[8];
     auto src = [&](int b, int n) MRDFT_INL -> float2 {
       const int base = b << i;
@@ -173,16 +175,24 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_tile(const FwdArgs a) {
     };
     auto pre = [&](int slot, int b, int k) MRDFT_INL {
       const int base = b << i;
-      ev[slot] = cadd(B[swz128(base + k)], B[swz128(base + h + k)]);  // U: child sum
+      ev[slot] = cadd(B[pad16(base + k)], B[pad16(base + h + k)]);  // U: child sum
     };
     auto sink = [&](int slot, int b, int k, float2 odd) MRDFT_INL {
       const int e = (b << i) + 2 * k;
       const float4 v = make_float4(ev[slot].x, ev[slot].y, odd.x, odd.y);
-      if (keep) st4s(B + swz128(e), v);
-      const TileSig& ts = TS[e >> tl];
-      float4* dst = reinterpret_cast<float4*>(a.y + ts.out_base + ((int64_t)(i - 1) << ts.m) + (e & ((1 << tl) - 1)));
-      // the tile's top level is re-read (children of level tl+1): keep it in L2
-      if (i == tl && ts.m > tl) __stcg(dst, v);
+      if (keep) {
+        const int pe = pad16(e);
+        B[pe] = ev[slot];
+        B[pe + 1] = odd;
+      }
+      float4* dst;
+      if (single) {
+        dst = reinterpret_cast<float4*>(ylev + e);
+      } else {
+        const TileSig& ts = TS[e >> tl];
+        dst = reinterpret_cast<float4*>(a.y + ts.out_base + ((int64_t)(i - 1) << ts.m) + (e & ((1 << tl) - 1)));
+      }
+      if (l2keep) __stcg(dst, v);
       else __stcs(dst, v);
     };
     cg_fft<4, TLOG - 1, NT, 8, false, true>(Z, i - 1, tn_log - i, tw, src, pre, sink);
@@ -211,39 +221,60 @@ __global__ void k_fwd_tiny(const FwdArgs a) {
 
 // =================================================================== window
 
-// One window of level i (13 <= i <= 14: h = 2^(i-1) = 2^12 or 2^13 odd-bin
-// DFT points) per CTA: z from x, DFT_h in shared memory, even bins from the
-// level-(i-1) children in y, (even, odd) pairs stored at 2k.
-__global__ void __launch_bounds__(kWinThreads) k_fwd_window(const FwdArgs a) {
+// One window of level i (h = 2^(i-1) <= 2^13 odd-bin DFT points) per CTA:
+// z from x, DFT_h in shared memory, even bins from the level-(i-1) children
+// in y (prefetched into registers before the last pass), (even, odd) pairs
+// stored at 2k.
+__global__ void __launch_bounds__(kWinThreads, 1) k_fwd_window(const FwdArgs a) {
   constexpr int NT = kWinThreads;
+  constexpr int PTS = (1 << kWinMaxLog) / NT;   // points per thread per pass
   extern __shared__ __align__(1024) float2 sm[];
-  float2* Z = sm;                               // 2^13 (pad8)
+  float2* Z = sm;                               // 2^13 (pad8; XOR layout while staging)
   float2* TQ = sm + pad8_size(1 << kWinMaxLog); // quarter-wave w_{2^13}
   if (blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
   const int i = a.level;
   const int LB = i - 1;
-  const int64_t h = (int64_t)1 << LB;
+  const int h = 1 << LB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t ws = (int64_t)it.window << i;
   const int64_t xs = sd.in_off + ws;
   const float2* yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
   load_twq<NT>(TQ, kWinMaxLog, a.tw);
+  // V (Eq. 3) and D: z[n] = (a[n] - b[n]) w_{2^i}^n; all loads of a thread are
+  // issued before any use, then z is staged in the XOR layout that the first
+  // FFT pass reads in digit-reversed order
+  {
+    float2 xa[PTS], xb[PTS], w[PTS];
+#pragma unroll
+    for (int q = 0; q < PTS; ++q) {
+      const int n = threadIdx.x + q * NT;
+      if (n < h) {
+        xa[q] = load_x1(a, xs + n);
+        xb[q] = load_x1(a, xs + h + n);
+        w[q] = tw_any(a.tw, i, n);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < PTS; ++q) {
+      const int n = threadIdx.x + q * NT;
+      if (n < h) Z[swzf(n)] = cmul(csub(xa[q], xb[q]), w[q]);
+    }
+  }
   __syncthreads();
   const TwQ tw{TQ, kWinMaxLog};
-  auto src = [&](int, int n) MRDFT_INL -> float2 {
-    return cmul(csub(load_x1(a, xs + n), load_x1(a, xs + h + n)), tw_any(a.tw, i, n));
-  };
   const bool reread = sd.m > i;  // children of the next level: keep in L2
-  auto sink = [&](int, int, int k, float2 odd) MRDFT_INL {
-    const float2 ev = cadd(__ldcg(yprev + k), __ldcg(yprev + h + k));
-    const float4 v = make_float4(ev.x, ev.y, odd.x, odd.y);
+  float2 ev[PTS];
+  auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[swzf(n)]; };
+  auto pre = [&](int slot, int, int k) MRDFT_INL { ev[slot] = cadd(__ldcg(yprev + k), __ldcg(yprev + h + k)); };
+  auto sink = [&](int slot, int, int k, float2 odd) MRDFT_INL {
+    const float4 v = make_float4(ev[slot].x, ev[slot].y, odd.x, odd.y);
     float4* dst = reinterpret_cast<float4*>(ycur + 2 * k);
     if (reread) __stcg(dst, v);
     else __stcs(dst, v);
   };
-  cg_fft<kTileLog, kWinMaxLog, NT, 32, false, false>(Z, LB, 0, tw, src, NoPre{}, sink);
+  cg_fft<kTileLog, kWinMaxLog, NT, PTS, false, true>(Z, LB, 0, tw, src, pre, sink);
 }
 
 // =============================================================== two-pass
@@ -271,21 +302,32 @@ __global__ void __launch_bounds__(kPassThreads) k_fwd_cols(const FwdArgs a) {
   const int r0 = it.block << RCB;
   const int64_t h = (int64_t)1 << HB;
   load_twq<NT>(TQ, kWinMaxLog, a.tw);
-  for (int e = threadIdx.x; e < RC * Q; e += NT) {
-    const int r = e & (RC - 1), q = e >> RCB;
-    const int64_t n = (int64_t)q * C + r0 + r;
-    const float2 z = cmul(csub(load_x1(a, xs + n), load_x1(a, xs + h + n)), tw_any(a.tw, i, n));
-    S[pad8(e)] = z;  // e = q RC + r
+#pragma unroll 1
+  for (int t0 = 0; t0 < kPassElems / NT; t0 += 8) {
+    // loads of a batch are all issued before any use
+    float2 xa[8], xb[8], w[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = threadIdx.x + (t0 + t) * NT;
+      const int r = e & (RC - 1), q = e >> RCB;
+      const int64_t n = (int64_t)q * C + r0 + r;
+      xa[t] = load_x1(a, xs + n);
+      xb[t] = load_x1(a, xs + h + n);
+      w[t] = tw_any(a.tw, i, n);
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t)  // e = q RC + r (XOR layout for the first pass)
+      S[swzf(threadIdx.x + (t0 + t) * NT)] = cmul(csub(xa[t], xb[t]), w[t]);
   }
   __syncthreads();
   const TwQ tw{TQ, kWinMaxLog};
   float2* G = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[pad8((n << RCB) + b)]; };
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((n << RCB) + b)]; };
   auto sink = [&](int, int b, int k2, float2 v) MRDFT_INL {
     const int r = r0 + b;
     __stcg(G + ((int64_t)k2 << CB) + r, cmul(v, tw_any(a.tw, HB, (int64_t)r * k2)));
   };
-  cg_fft<2, kWinMaxLog, NT, 32, true, false>(S, QB, RCB, tw, src, NoPre{}, sink);
+  cg_fft<2, kWinMaxLog, NT, kPassElems / NT, true, false>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
 // rows: item (sig, window, block) covers residues k2 in [k0, k0 + KC),
@@ -308,19 +350,21 @@ __global__ void __launch_bounds__(kPassThreads) k_fwd_rows(const FwdArgs a) {
   const int k0 = it.block << KCB;
   const float2* G = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
   load_twq<NT>(TQ, CB, a.tw);
-#pragma unroll 4
+#pragma unroll 8
   for (int e = threadIdx.x; e < KC * C; e += NT) {
     const int r = e & (C - 1), j = e >> CB;
-    S[pad8((r << KCB) + j)] = __ldcg(G + ((int64_t)(k0 + j) << CB) + r);
+    cp_async8(S + swzf((r << KCB) + j), G + ((int64_t)(k0 + j) << CB) + r);
   }
+  cp_async_wait_all();
   __syncthreads();
   // the intermediate rows are dead now: drop them from L2 without write-back
   for (int l = threadIdx.x; l < KC * C / 16; l += NT) discard_l2(G + ((int64_t)k0 << CB) + 16 * l);
   const TwQ tw{TQ, CB};
   const float2* yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[pad8((n << KCB) + b)]; };
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((n << KCB) + b)]; };
   const bool reread = sd.m > i;
+  constexpr int PTS = kPassElems / NT;
   auto sink = [&](int, int b, int k1, float2 odd) MRDFT_INL {
     const int64_t k = ((int64_t)k1 << QB) + k0 + b;
     const float2 ev = cadd(__ldcg(yprev + k), __ldcg(yprev + h + k));
@@ -329,13 +373,15 @@ __global__ void __launch_bounds__(kPassThreads) k_fwd_rows(const FwdArgs a) {
     if (reread) __stcg(dst, v);
     else __stcs(dst, v);
   };
-  cg_fft<CB, CB, NT, 32, true, false>(S, CB, KCB, tw, src, NoPre{}, sink);
+  cg_fft<CB, CB, NT, PTS, true, false>(S, CB, KCB, tw, src, NoPre{}, sink);
 }
 
 // ================================================================ launchers
 
-static constexpr size_t kTileSmem = (size_t)(2 * kTile + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kMaxPack * sizeof(TileSig);
+static constexpr size_t kTileSmem =
+    (size_t)(kTile + pad16_size(kTile) + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kMaxPack * sizeof(TileSig);
 static constexpr size_t kWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog)) * sizeof(float2);
+static_assert(kPassElems % kPassThreads == 0 && (1 << kWinMaxLog) % kWinThreads == 0, "points per thread");
 static constexpr size_t kPassSmem = (size_t)(pad8_size(kPassElems) + twq_size(kWinMaxLog)) * sizeof(float2);
 
 cudaError_t set_fwd_attributes() {

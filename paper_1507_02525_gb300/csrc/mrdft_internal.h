@@ -37,11 +37,11 @@ struct LevelItem {
   int32_t pad;
 };
 
-constexpr int kTileLog = 12;                 // in-tile levels 1..12
-constexpr int kTile = 1 << kTileLog;         // 4096 samples per tile
-constexpr int kTileThreads = 256;            // 16 samples per thread
+constexpr int kTileLog = 13;                 // in-tile levels 1..13
+constexpr int kTile = 1 << kTileLog;         // 8192 samples per tile
+constexpr int kTileThreads = 512;            // 16 samples per thread
 constexpr int kWinMaxLog = 13;               // one CTA FFT holds up to 2^13 points
-constexpr int kWinThreads = 256;
+constexpr int kWinThreads = 512;
 constexpr int kColsLog = 12;                 // two-pass levels: FFT_C over 2^12 ...
 constexpr int kPassElems = 1 << 14;          // ... and 2^14 points of smem per CTA
 constexpr int kPassThreads = 512;
