@@ -154,6 +154,29 @@ mrdft_status mrdft_timing_enable(mrdft_plan_t plan, int enable);
 mrdft_status mrdft_timing_read(mrdft_plan_t plan, int kind, double* ms, int64_t* launches,
                                int64_t* bytes);
 
+/*
+ * mrdft_forward_noalloc -- forward MrDFT of ONE complex64 signal of length n
+ * (a power of two, 2 <= n <= 2^MRDFT_NOALLOC_MAX_LOG) without any plan and
+ * without allocating: the paper has no counterpart; this entry point exists
+ * for callers that must not call cudaMalloc -- code that runs under an
+ * external memory manager owning every device allocation, or inside a loop
+ * where an allocation's implicit device synchronisation is not acceptable.
+ *   x : device input, n complex64;  y : device output, log2(n) * n complex64
+ *       (levels ascending, as for mrdft_forward);  stream : CUDA stream.
+ * The intermediate of the two-pass levels (15 and 16) lives in a fixed
+ * device array of 2^(MRDFT_NOALLOC_MAX_LOG - 1) complex64 (256 KiB), which
+ * every GPU that loads this library keeps until the process exits, next to
+ * the twiddle tables and work lists (about 350 KiB in all).  The first call
+ * on a device sets that storage up (symbol addresses, tables copied from the
+ * host) and synchronises with the device; make that first call before any
+ * stream capture.  Every call shares the same storage, so calls whose work
+ * overlaps on the GPU (different streams, or different host threads) race
+ * and give wrong results; calls on one stream are ordered and safe.  Sizes
+ * above the limit return MRDFT_EINVAL with a message (mrdft_last_error(NULL)).
+ */
+#define MRDFT_NOALLOC_MAX_LOG 16
+mrdft_status mrdft_forward_noalloc(const void* x, void* y, int64_t n, mrdft_stream_t stream);
+
 /* Release everything the plan owns.  NULL is ignored. */
 void mrdft_destroy(mrdft_plan_t plan);
 

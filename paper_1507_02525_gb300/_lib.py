@@ -30,7 +30,9 @@ STATUS_NAMES = {0: "MRDFT_OK", 1: "MRDFT_EINVAL", 2: "MRDFT_ENOMEM", 3: "MRDFT_E
 # every entry point declared in include/mrdft.h
 EXPORTS = ("mrdft_plan", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
            "mrdft_adjoint", "mrdft_forward_host", "mrdft_status_poll", "mrdft_last_error",
-           "mrdft_plan_info", "mrdft_timing_enable", "mrdft_timing_read", "mrdft_destroy")
+           "mrdft_plan_info", "mrdft_timing_enable", "mrdft_timing_read", "mrdft_forward_noalloc",
+           "mrdft_destroy")
+NOALLOC_MAX_LOG = 16
 
 KINDS = ("fwd_tile", "fwd_tiny", "fwd_window", "fwd_cols", "fwd_rows",
          "adj_tile", "adj_tiny", "adj_window", "adj_rows", "adj_cols")
@@ -75,6 +77,8 @@ def load(build_if_missing: bool = True):
         lib.mrdft_timing_enable.argtypes = [vp, i32]
         lib.mrdft_timing_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.mrdft_forward_noalloc.argtypes = [vp, vp, i64, vp]
+        lib.mrdft_forward_noalloc.restype = ctypes.c_int
         lib.mrdft_destroy.argtypes = [vp]
         lib.mrdft_destroy.restype = None
         for name in ("mrdft_plan", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
@@ -83,6 +87,13 @@ def load(build_if_missing: bool = True):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
+
+
+def forward_noalloc(x_ptr: int, y_ptr: int, n: int, stream: int = 0) -> None:
+    """mrdft_forward_noalloc: one complex64 signal, no plan, no allocation."""
+    lib = load()
+    check(lib.mrdft_forward_noalloc(ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr), int(n),
+                                    ctypes.c_void_p(stream)), None)
 
 
 def check(status: int, plan=None) -> None:

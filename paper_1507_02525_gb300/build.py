@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libmrdft.so")
-SOURCES = ["mrdft_fwd.cu", "mrdft_adj.cu", "mrdft_plan.cu"]
+SOURCES = ["mrdft_fwd.cu", "mrdft_adj.cu", "mrdft_plan.cu", "mrdft_static.cu"]
 HEADERS = ["mrdft_common.cuh", "mrdft_fft.cuh", "mrdft_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",

@@ -25,6 +25,7 @@
 namespace mrdft {
 cudaError_t set_fwd_attributes();
 cudaError_t set_adj_attributes();
+void set_global_error(const std::string& msg);
 }  // namespace mrdft
 
 using namespace mrdft;
@@ -67,6 +68,11 @@ std::mutex g_err_mu;
 std::string g_global_err = "no error";
 
 }  // namespace
+
+void mrdft::set_global_error(const std::string& msg) {
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_global_err = msg;
+}
 
 struct mrdft_plan_s {
   int device = 0;
