@@ -236,18 +236,18 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_adj_window(const AdjArgs a) 
   const int h = 1 << LB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
-  load_twq<NT>(TQ, kWinMaxLog, a.tw);
+  load_twq<NT>(TQ, kWinMaxLog + 1, a.tw);
   for (int k = threadIdx.x; k < h; k += NT) {
     const float4 g = adj_G(a, sd, i, w, 2 * (int64_t)k);
     __stcg(a.e_out + sd.aux_off + (w << LB) + k, make_float2(g.x, g.y));
     Z[swzf(k)] = make_float2(g.z, -g.w);
   }
   __syncthreads();
-  const TwQ tw{TQ, kWinMaxLog};
+  const TwQ tw{TQ, kWinMaxLog + 1};
   const int64_t ws = w << i;
   auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[swzf(n)]; };
   auto sink = [&](int, int, int n, float2 v) MRDFT_INL {
-    const float2 c = cmulc(conjf2(v), tw_any(a.tw, i, n));
+    const float2 c = cmulc(conjf2(v), twq_l(tw, i, n));
     acc_add(a, sd, i, ws + n, c);
     acc_add(a, sd, i, ws + h + n, make_float2(-c.x, -c.y));
   };
@@ -256,99 +256,133 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_adj_window(const AdjArgs a) 
 
 // =============================================================== two-pass
 
-// Adjoint of the forward two-pass level (h = Q * C, C = 2^12).
-// rows: item (sig, window, block) covers residues k2 in [k0, k0 + 4):
-//   G odd bins k = Q k1 + k2 -> IDFT_C over k1 -> times conj(w_h^(r k2))
-//   -> scratch U[window][k2][r]; even bins -> e_out.
-__global__ void __launch_bounds__(kPassThreads) k_adj_rows(const AdjArgs a) {
-  constexpr int NT = kPassThreads;
-  constexpr int CB = kColsLog, C = 1 << CB;
-  constexpr int KCB = 14 - CB, KC = 1 << KCB;
+// Adjoint of the forward two-pass level (h = Q * C, C = 2^cols_log(i)).
+// rows: item (sig, window, block) covers residues k2 in [k0, k0 + KC),
+//   KC = 2^13 / C: odd-bin gradients at k = Q k1 + k2 -> IDFT_C over k1 ->
+//   times conj(w_h^(r k2)) -> scratch U[window][k2][r]; even bins -> e_out.
+__global__ void __launch_bounds__(kRowsThreads, 1) k_adj_rows(const AdjArgs a) {
+  constexpr int NT = kRowsThreads;
+  constexpr int E = kRowsElemsLog;
   extern __shared__ __align__(1024) float2 sm[];
-  float2* S = sm;                               // sequence j at j C (pad8)
-  float2* TQ = sm + pad8_size(kPassElems);
+  float2* S = sm;                          // sequence j at j C (XOR, then pad8)
+  float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^13}
+  float2* TWL = TQ + twq_size(13);         // [KC][64] (row stride 65): w_h^(k2 t)
+  float2* TWH = TWL + 4 * 65;              // [KC][C/64] (row stride C/64 + 1): w_h^(k2 64 u)
   if (blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
   const int i = a.level;
-  const int HB = i - 1, QB = HB - CB;
+  const int HB = i - 1, CB = cols_log(i), QB = HB - CB;
+  const int KCB = E - CB, KC = 1 << KCB;
+  const int HU = (1 << CB) >> 6;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
   const int k0 = it.block << KCB;
-  load_twq<NT>(TQ, CB, a.tw);
-  for (int e = threadIdx.x; e < KC * C; e += NT) {
-    const int j = e & (KC - 1), k1 = e >> KCB;
-    const int64_t k = ((int64_t)k1 << QB) + k0 + j;
-    const float4 g = adj_G(a, sd, i, w, 2 * k);
-    __stcg(a.e_out + sd.aux_off + (w << HB) + k, make_float2(g.x, g.y));
-    S[swzf((j << CB) + k1)] = make_float2(g.z, -g.w);
+  // gradient pairs (2k, 2k+1): a batch of loads is issued before any store
+#pragma unroll 1
+  for (int t0 = 0; t0 < (1 << E) / NT; t0 += 8) {
+    float4 g[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = threadIdx.x + (t0 + t) * NT;
+      const int64_t k = ((int64_t)(e >> KCB) << QB) + k0 + (e & (KC - 1));
+      g[t] = adj_G(a, sd, i, w, 2 * k);
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = threadIdx.x + (t0 + t) * NT;
+      const int j = e & (KC - 1), k1 = e >> KCB;
+      const int64_t k = ((int64_t)k1 << QB) + k0 + j;
+      __stcg(a.e_out + sd.aux_off + (w << HB) + k, make_float2(g[t].x, g[t].y));
+      S[swzf((j << CB) + k1)] = make_float2(g[t].z, -g[t].w);
+    }
+  }
+  load_twq<NT>(TQ, 13, a.tw);
+  for (int t = threadIdx.x; t < KC * (64 + HU); t += NT) {
+    if (t < KC * 64) {
+      const int j = t >> 6, u = t & 63;
+      TWL[j * 65 + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * u);
+    } else {
+      const int t2 = t - KC * 64, j = t2 / HU, u = t2 % HU;
+      TWH[j * (HU + 1) + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * 64 * u);
+    }
   }
   __syncthreads();
-  const TwQ tw{TQ, CB};
+  const TwQ tw{TQ, 13};
   float2* U = a.scratch + sd.aux_off + (w << HB);
   auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((b << CB) + n)]; };
   auto sink = [&](int, int b, int r, float2 v) MRDFT_INL {
-    const int k2 = k0 + b;
-    __stcg(U + ((int64_t)k2 << CB) + r, cmulc(conjf2(v), tw_any(a.tw, HB, (int64_t)r * k2)));
+    const float2 t = cmul(TWL[b * 65 + (r & 63)], TWH[b * (HU + 1) + (r >> 6)]);
+    __stcg(U + ((int64_t)(k0 + b) << CB) + r, cmulc(conjf2(v), t));
   };
-  cg_fft<CB, CB, NT, kPassElems / NT, false, false>(S, CB, KCB, tw, src, NoPre{}, sink);
+  cg_fft<11, 13, NT, (1 << E) / NT, false, false>(S, CB, KCB, tw, src, NoPre{}, sink);
 }
 
-// cols: item (sig, window, block) covers chunk offsets r in [r0, r0 + RC):
-//   U[window][k2][r] -> IDFT_Q over k2 -> zb[r + C q] -> conj(w_{2^i}^n) zb
-//   added to acc at n and subtracted at h + n.
-__global__ void __launch_bounds__(kPassThreads) k_adj_cols(const AdjArgs a) {
-  constexpr int NT = kPassThreads;
-  constexpr int CB = kColsLog;
+// cols: item (sig, window, 2 c) covers chunk offsets r in [r0, r0 + RC),
+//   r0 = c RC, RC = 2^14 / Q: U[window][k2][r] -> IDFT_Q over k2 -> zb[r + C q]
+//   -> conj(w_{2^i}^n) zb added to acc at n and subtracted at h + n.
+__global__ void __launch_bounds__(kColsThreads, 1) k_adj_cols(const AdjArgs a) {
+  constexpr int NT = kColsThreads;
+  constexpr int E = kColsElemsLog;
   extern __shared__ __align__(1024) float2 sm[];
-  float2* S = sm;                               // column r position k2 at k2 RC + r (pad8)
-  float2* TQ = sm + pad8_size(kPassElems);
-  if (blockIdx.x >= a.nitems) return;
-  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  float2* S = sm;                          // column r position k2 at k2 RC + r (XOR, then pad8)
+  float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^13}
+  float2* ZC = TQ + twq_size(13);          // w_{2^i}^(r0 + r), r < RC
+  if (2 * (int)blockIdx.x >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[2 * blockIdx.x];
   const int i = a.level;
-  const int HB = i - 1, QB = HB - CB;
-  const int RCB = 14 - QB, RC = 1 << RCB;
-  const int Q = 1 << QB;
+  const int HB = i - 1, CB = cols_log(i), QB = HB - CB;
+  const int RCB = E - QB, RC = 1 << RCB;
   const int64_t h = (int64_t)1 << HB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
-  const int r0 = it.block << RCB;
+  const int r0 = (it.block >> 1) << RCB;
   const float2* U = a.scratch + sd.aux_off + (w << HB);
-  load_twq<NT>(TQ, kWinMaxLog, a.tw);
-#pragma unroll 4
-  for (int e = threadIdx.x; e < RC * Q; e += NT) {
-    const int r = e & (RC - 1), k2 = e >> RCB;
-    S[swzf(e)] = conjf2(__ldcg(U + ((int64_t)k2 << CB) + r0 + r));  // e = k2 RC + r
+#pragma unroll 1
+  for (int t0 = 0; t0 < (1 << E) / NT; t0 += 8) {
+    float2 u[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int e = threadIdx.x + (t0 + t) * NT;
+      u[t] = __ldcg(U + ((int64_t)(e >> RCB) << CB) + r0 + (e & (RC - 1)));
+    }
+#pragma unroll
+    for (int t = 0; t < 8; ++t) S[swzf(threadIdx.x + (t0 + t) * NT)] = conjf2(u[t]);  // e = k2 RC + r
   }
+  load_twq<NT>(TQ, 13, a.tw);
+  for (int r = threadIdx.x; r < RC; r += NT) ZC[r] = tw_any(a.tw, i, r0 + r);
   __syncthreads();
   // this block's columns of the intermediate are dead: drop them from L2
   if (RC >= 16)
-    for (int l = threadIdx.x; l < Q * (RC / 16); l += NT)
-      discard_l2(U + ((int64_t)(l / (RC / 16)) << CB) + r0 + 16 * (l % (RC / 16)));
-  const TwQ tw{TQ, kWinMaxLog};
+    for (int l = threadIdx.x; l < (RC / 16) << QB; l += NT)
+      discard_l2(U + ((int64_t)(l >> (RCB - 4)) << CB) + r0 + 16 * (l & ((RC / 16) - 1)));
+  const TwQ tw{TQ, 13};
   const int64_t ws = w << i;
   auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((n << RCB) + b)]; };
   auto sink = [&](int, int b, int q, float2 v) MRDFT_INL {
     const int64_t n = ((int64_t)q << CB) + r0 + b;
-    const float2 c = cmulc(conjf2(v), tw_any(a.tw, i, n));
+    const float2 c = cmulc(conjf2(v), cmul(ZC[b], twq_l(tw, QB + 1, q)));
     acc_add(a, sd, i, ws + n, c);
     acc_add(a, sd, i, ws + h + n, make_float2(-c.x, -c.y));
   };
-  cg_fft<2, kWinMaxLog, NT, kPassElems / NT, true, false>(S, QB, RCB, tw, src, NoPre{}, sink);
+  cg_fft<3, 12, NT, (1 << E) / NT, true, false>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
 // ================================================================ launchers
 
 static constexpr size_t kAdjTileSmem =
     (size_t)(2 * kTile + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kAdjMaxPack * sizeof(AdjTileSig);
-static constexpr size_t kAdjWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog)) * sizeof(float2);
-static constexpr size_t kAdjPassSmem = (size_t)(pad8_size(kPassElems) + twq_size(kWinMaxLog)) * sizeof(float2);
+static constexpr size_t kAdjWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog + 1)) * sizeof(float2);
+static constexpr size_t kAdjColsSmem =
+    (size_t)(pad8_size(1 << kColsElemsLog) + twq_size(13) + (1 << (kColsElemsLog - 3))) * sizeof(float2);
+static constexpr size_t kAdjRowsSmem =
+    (size_t)(pad8_size(1 << kRowsElemsLog) + twq_size(13) + 4 * 65 + 4 * 33) * sizeof(float2);
 
 cudaError_t set_adj_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_adj_tile<kTileLog, kTileThreads>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjTileSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjPassSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjPassSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjRowsSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjColsSmem);
   return e;
 }
 
@@ -365,11 +399,11 @@ cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s) {
-  k_adj_rows<<<grid, kPassThreads, kAdjPassSmem, s>>>(a);
+  k_adj_rows<<<grid, kRowsThreads, kAdjRowsSmem, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_adj_cols(const AdjArgs& a, int grid, cudaStream_t s) {
-  k_adj_cols<<<grid, kPassThreads, kAdjPassSmem, s>>>(a);
+  k_adj_cols<<<(grid + 1) / 2, kColsThreads, kAdjColsSmem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -138,8 +138,8 @@ __device__ __forceinline__ int swzf(int e) { return e ^ (((e >> 4) ^ (e >> 8)) &
 
 // ------------------------------------------------------------ twiddle tables
 // Device tables written once by the plan from FP64 host values rounded once:
-//   tw13[e] = w_{2^13}^e, e < 2^13   (every FFT of length <= 2^13 and the
-//                                       level twiddles w_{2^i}^n, i <= 13)
+//   tw13[e] = w_{2^14}^e, e < 2^14   (every FFT of length <= 2^14 and the
+//                                       level twiddles w_{2^i}^n, i <= 14)
 //   twlo[e] = w_{2^28}^e, e < 2^14 and twhi[e] = w_{2^28}^{e * 2^14},
 //   e < 2^14: w_{2^28}^e = twhi[e >> 14] * twlo[e & 16383] for larger levels
 //   (the product of two once-rounded values: one extra FP32 rounding).
@@ -148,7 +148,7 @@ struct Twiddles {
   const float2* twlo;
   const float2* twhi;
 };
-constexpr int kTwLog = 13;
+constexpr int kTwLog = 14;
 constexpr int kTwBigLog = 28;
 constexpr int kTwSplit = 14;
 

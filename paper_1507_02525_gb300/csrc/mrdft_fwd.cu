@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_fwd_window(const FwdArgs a) 
   constexpr int PTS = (1 << kWinMaxLog) / NT;   // points per thread per pass
   extern __shared__ __align__(1024) float2 sm[];
   float2* Z = sm;                               // 2^13 (pad8; XOR layout while staging)
-  float2* TQ = sm + pad8_size(1 << kWinMaxLog); // quarter-wave w_{2^13}
+  float2* TQ = sm + pad8_size(1 << kWinMaxLog); // quarter-wave w_{2^14}
   if (blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
   const int i = a.level;
@@ -241,29 +241,29 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_fwd_window(const FwdArgs a) 
   const int64_t xs = sd.in_off + ws;
   const float2* yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
-  load_twq<NT>(TQ, kWinMaxLog, a.tw);
+  load_twq<NT>(TQ, kWinMaxLog + 1, a.tw);
+  __syncthreads();
+  const TwQ tw{TQ, kWinMaxLog + 1};
   // V (Eq. 3) and D: z[n] = (a[n] - b[n]) w_{2^i}^n; all loads of a thread are
   // issued before any use, then z is staged in the XOR layout that the first
   // FFT pass reads in digit-reversed order
   {
-    float2 xa[PTS], xb[PTS], w[PTS];
+    float2 xa[PTS], xb[PTS];
 #pragma unroll
     for (int q = 0; q < PTS; ++q) {
       const int n = threadIdx.x + q * NT;
       if (n < h) {
         xa[q] = load_x1(a, xs + n);
         xb[q] = load_x1(a, xs + h + n);
-        w[q] = tw_any(a.tw, i, n);
       }
     }
 #pragma unroll
     for (int q = 0; q < PTS; ++q) {
       const int n = threadIdx.x + q * NT;
-      if (n < h) Z[swzf(n)] = cmul(csub(xa[q], xb[q]), w[q]);
+      if (n < h) Z[swzf(n)] = cmul(csub(xa[q], xb[q]), twq_l(tw, i, n));
     }
   }
   __syncthreads();
-  const TwQ tw{TQ, kWinMaxLog};
   const bool reread = sd.m > i;  // children of the next level: keep in L2
   float2 ev[PTS];
   auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[swzf(n)]; };
@@ -279,117 +279,142 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_fwd_window(const FwdArgs a) 
 
 // =============================================================== two-pass
 
-// Level i with h = 2^(i-1) = Q * C, C = 2^12, Q = 2^(i-13).
-// cols: item (sig, window, block) covers chunk offsets r in [r0, r0 + RC),
-//   RC = 2^14 / Q.  z[r + C q] (q < Q) -> DFT_Q over q -> times w_h^(r k2)
-//   -> scratch G[window][k2][r].
-__global__ void __launch_bounds__(kPassThreads) k_fwd_cols(const FwdArgs a) {
-  constexpr int NT = kPassThreads;
-  constexpr int CB = kColsLog, C = 1 << CB;
+// Level i with h = 2^(i-1) = Q * C, C = 2^CB (cols_log), Q = 2^QB.
+// With n = r + C q (r < C, q < Q) and k = Q k1 + k2:
+//   DFT_h(z)[Q k1 + k2] = sum_r w_C^(r k1) w_h^(r k2) sum_q z[r + C q] w_Q^(q k2).
+// cols: item (sig, window, 2 c) covers chunk offsets r in [r0, r0 + RC),
+//   r0 = c RC, RC = 2^14 / Q: z[r + C q] -> DFT_Q over q -> scratch F[window][k2][r].
+// rows: item covers residues k2 in [k0, k0 + KC), KC = 2^13 / C:
+//   F[window][k2][.] times w_h^(r k2) -> DFT_C -> odd bin Q k1 + k2; even bin
+//   from the children; (even, odd) pairs stored at 2k.
+__global__ void __launch_bounds__(kColsThreads, 1) k_fwd_cols(const FwdArgs a) {
+  constexpr int NT = kColsThreads;
+  constexpr int E = kColsElemsLog;
   extern __shared__ __align__(1024) float2 sm[];
-  float2* S = sm;                       // 2^14 (pad8), column r position q at q RC + r
-  float2* TQ = sm + pad8_size(kPassElems);  // quarter-wave w_{2^13}
-  if (blockIdx.x >= a.nitems) return;
-  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  float2* S = sm;                            // column r position q: q RC + r (XOR, then pad8)
+  float2* TQ = sm + pad8_size(1 << E);       // quarter-wave w_{2^13}
+  float2* ZC = TQ + twq_size(13);            // w_{2^i}^(r0 + r), r < RC
+  if (2 * (int)blockIdx.x >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[2 * blockIdx.x];
   const int i = a.level;
-  const int HB = i - 1, QB = HB - CB;
-  const int RCB = 14 - QB;
-  const int RC = 1 << RCB;
-  const int Q = 1 << QB;
+  const int HB = i - 1, CB = cols_log(i), QB = HB - CB;
+  const int C = 1 << CB;
+  const int RCB = E - QB, RC = 1 << RCB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t ws = (int64_t)it.window << i;
   const int64_t xs = sd.in_off + ws;
-  const int r0 = it.block << RCB;
+  const int r0 = (it.block >> 1) << RCB;
   const int64_t h = (int64_t)1 << HB;
-  load_twq<NT>(TQ, kWinMaxLog, a.tw);
+  load_twq<NT>(TQ, 13, a.tw);
+  for (int r = threadIdx.x; r < RC; r += NT) ZC[r] = tw_any(a.tw, i, r0 + r);
+  __syncthreads();
+  const TwQ tw{TQ, 13};
+  // V (Eq. 3) and D: z[n] = (a[n] - b[n]) w_{2^i}^n, w_{2^i}^(r0 + r + C q) =
+  // w_{2^i}^(r0 + r) w_{2Q}^q; loads of a batch issued before any use
 #pragma unroll 1
-  for (int t0 = 0; t0 < kPassElems / NT; t0 += 8) {
-    // loads of a batch are all issued before any use
-    float2 xa[8], xb[8], w[8];
+  for (int t0 = 0; t0 < (1 << E) / NT; t0 += 8) {
+    float2 xa[8], xb[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int e = threadIdx.x + (t0 + t) * NT;
-      const int r = e & (RC - 1), q = e >> RCB;
-      const int64_t n = (int64_t)q * C + r0 + r;
+      const int64_t n = ((int64_t)(e >> RCB) << CB) + r0 + (e & (RC - 1));
       xa[t] = load_x1(a, xs + n);
       xb[t] = load_x1(a, xs + h + n);
-      w[t] = tw_any(a.tw, i, n);
     }
 #pragma unroll
-    for (int t = 0; t < 8; ++t)  // e = q RC + r (XOR layout for the first pass)
-      S[swzf(threadIdx.x + (t0 + t) * NT)] = cmul(csub(xa[t], xb[t]), w[t]);
+    for (int t = 0; t < 8; ++t) {
+      const int e = threadIdx.x + (t0 + t) * NT;
+      const float2 w = cmul(ZC[e & (RC - 1)], twq_l(tw, QB + 1, e >> RCB));
+      S[swzf(e)] = cmul(csub(xa[t], xb[t]), w);  // e = q RC + r
+    }
   }
   __syncthreads();
-  const TwQ tw{TQ, kWinMaxLog};
-  float2* G = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
+  float2* F = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
   auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((n << RCB) + b)]; };
-  auto sink = [&](int, int b, int k2, float2 v) MRDFT_INL {
-    const int r = r0 + b;
-    __stcg(G + ((int64_t)k2 << CB) + r, cmul(v, tw_any(a.tw, HB, (int64_t)r * k2)));
-  };
-  cg_fft<2, kWinMaxLog, NT, kPassElems / NT, true, false>(S, QB, RCB, tw, src, NoPre{}, sink);
+  auto sink = [&](int, int b, int k2, float2 v) MRDFT_INL { __stcg(F + ((int64_t)k2 << CB) + r0 + b, v); };
+  cg_fft<3, 12, NT, (1 << E) / NT, true, false>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
-// rows: item (sig, window, block) covers residues k2 in [k0, k0 + KC),
-//   KC = 2^14 / C = 4.  G[window][k2][0..C) -> DFT_C -> odd bin k = Q k1 + k2,
-//   even bin from the children; (even, odd) pairs stored at 2k.
-__global__ void __launch_bounds__(kPassThreads) k_fwd_rows(const FwdArgs a) {
-  constexpr int NT = kPassThreads;
-  constexpr int CB = kColsLog, C = 1 << CB;
-  constexpr int KCB = 14 - CB, KC = 1 << KCB;
+__global__ void __launch_bounds__(kRowsThreads, 1) k_fwd_rows(const FwdArgs a) {
+  constexpr int NT = kRowsThreads;
+  constexpr int E = kRowsElemsLog;
+  constexpr int PTS = (1 << E) / NT;
   extern __shared__ __align__(1024) float2 sm[];
-  float2* S = sm;                          // sequence j position r at r KC + j (pad8)
-  float2* TQ = sm + pad8_size(kPassElems);
+  float2* S = sm;                          // sequence j position r at r KC + j (XOR, then pad8)
+  float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^13}
+  float2* TWL = TQ + twq_size(13);         // [KC][64] (row stride 65): w_h^(k2 t)
+  float2* TWH = TWL + 4 * 65;              // [KC][C/64] (row stride C/64 + 1): w_h^(k2 64 u)
   if (blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
   const int i = a.level;
-  const int HB = i - 1, QB = HB - CB;
+  const int HB = i - 1, CB = cols_log(i), QB = HB - CB;
+  const int C = 1 << CB;
+  const int KCB = E - CB, KC = 1 << KCB;
+  const int HU = C >> 6;                   // rows of the high twiddle table
   const int64_t h = (int64_t)1 << HB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t ws = (int64_t)it.window << i;
   const int k0 = it.block << KCB;
-  const float2* G = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
-  load_twq<NT>(TQ, CB, a.tw);
+  const float2* F = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
 #pragma unroll 8
   for (int e = threadIdx.x; e < KC * C; e += NT) {
     const int r = e & (C - 1), j = e >> CB;
-    cp_async8(S + swzf((r << KCB) + j), G + ((int64_t)(k0 + j) << CB) + r);
+    cp_async8(S + swzf((r << KCB) + j), F + ((int64_t)(k0 + j) << CB) + r);
+  }
+  load_twq<NT>(TQ, 13, a.tw);
+  for (int t = threadIdx.x; t < KC * (64 + HU); t += NT) {
+    if (t < KC * 64) {
+      const int j = t >> 6, u = t & 63;
+      TWL[j * 65 + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * u);
+    } else {
+      const int t2 = t - KC * 64, j = t2 / HU, u = t2 % HU;
+      TWH[j * (HU + 1) + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * 64 * u);
+    }
   }
   cp_async_wait_all();
   __syncthreads();
   // the intermediate rows are dead now: drop them from L2 without write-back
-  for (int l = threadIdx.x; l < KC * C / 16; l += NT) discard_l2(G + ((int64_t)k0 << CB) + 16 * l);
-  const TwQ tw{TQ, CB};
+  for (int l = threadIdx.x; l < KC * C / 16; l += NT) discard_l2(F + ((int64_t)k0 << CB) + 16 * l);
+  const TwQ tw{TQ, 13};
   const float2* yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((n << KCB) + b)]; };
+  // w_h^(r k2) = w_h^(k2 (r mod 64)) w_h^(k2 64 (r / 64))
+  auto src = [&](int b, int n) MRDFT_INL -> float2 {
+    return cmul(S[swzf((n << KCB) + b)], cmul(TWL[b * 65 + (n & 63)], TWH[b * (HU + 1) + (n >> 6)]));
+  };
   const bool reread = sd.m > i;
-  constexpr int PTS = kPassElems / NT;
-  auto sink = [&](int, int b, int k1, float2 odd) MRDFT_INL {
+  float2 ev[PTS];
+  auto pre = [&](int slot, int b, int k1) MRDFT_INL {
     const int64_t k = ((int64_t)k1 << QB) + k0 + b;
-    const float2 ev = cadd(__ldcg(yprev + k), __ldcg(yprev + h + k));
-    const float4 v = make_float4(ev.x, ev.y, odd.x, odd.y);
+    ev[slot] = cadd(__ldcg(yprev + k), __ldcg(yprev + h + k));
+  };
+  auto sink = [&](int slot, int b, int k1, float2 odd) MRDFT_INL {
+    const int64_t k = ((int64_t)k1 << QB) + k0 + b;
+    const float4 v = make_float4(ev[slot].x, ev[slot].y, odd.x, odd.y);
     float4* dst = reinterpret_cast<float4*>(ycur + 2 * k);
     if (reread) __stcg(dst, v);
     else __stcs(dst, v);
   };
-  cg_fft<CB, CB, NT, PTS, true, false>(S, CB, KCB, tw, src, NoPre{}, sink);
+  cg_fft<11, 13, NT, PTS, true, true>(S, CB, KCB, tw, src, pre, sink);
 }
 
 // ================================================================ launchers
 
 static constexpr size_t kTileSmem =
     (size_t)(kTile + pad16_size(kTile) + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kMaxPack * sizeof(TileSig);
-static constexpr size_t kWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog)) * sizeof(float2);
-static_assert(kPassElems % kPassThreads == 0 && (1 << kWinMaxLog) % kWinThreads == 0, "points per thread");
-static constexpr size_t kPassSmem = (size_t)(pad8_size(kPassElems) + twq_size(kWinMaxLog)) * sizeof(float2);
+static constexpr size_t kWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog + 1)) * sizeof(float2);
+static_assert((1 << kWinMaxLog) % kWinThreads == 0, "points per thread");
+static constexpr size_t kColsSmem =
+    (size_t)(pad8_size(1 << kColsElemsLog) + twq_size(13) + (1 << (kColsElemsLog - 3))) * sizeof(float2);
+// twiddle tables: KC (64 + 1) + KC (C / 64 + 1) <= 4 * 65 + 4 * 33 for every C = 2^13 / KC >= 2^11
+static constexpr size_t kRowsSmem = (size_t)(pad8_size(1 << kRowsElemsLog) + twq_size(13) + 4 * 65 + 4 * 33) * sizeof(float2);
 
 cudaError_t set_fwd_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_fwd_tile<kTileLog, kTileThreads>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPassSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColsSmem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowsSmem);
   return e;
 }
 
@@ -406,11 +431,11 @@ cudaError_t launch_fwd_window(const FwdArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s) {
-  k_fwd_cols<<<grid, kPassThreads, kPassSmem, s>>>(a);
+  k_fwd_cols<<<(grid + 1) / 2, kColsThreads, kColsSmem, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_rows(const FwdArgs& a, int grid, cudaStream_t s) {
-  k_fwd_rows<<<grid, kPassThreads, kPassSmem, s>>>(a);
+  k_fwd_rows<<<grid, kRowsThreads, kRowsSmem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -309,7 +309,7 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
   std::vector<int32_t> tile_ids;
   std::vector<TileItem> tiles;
   std::vector<LevelItem> litems;
-  auto pass_blocks = [](int i) { return std::max(1, (1 << (i - 1 - kColsLog)) / 4); };
+  auto pass_blocks = [](int i) { return pass_items(i); };
   auto add_level_items = [&](int i, int32_t sig, int64_t w0, int64_t nw, Launch& L) {
     const int nblk = i <= kWinMaxLog + 1 ? 1 : pass_blocks(i);
     for (int64_t w = w0; w < w0 + nw; ++w)

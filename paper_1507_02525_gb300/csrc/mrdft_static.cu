@@ -114,7 +114,7 @@ cudaError_t setup(DevState& st) {
     int off = 0;
     for (int i = kTileLog + 1; i <= m; ++i) {
       const int nw = 1 << (m - i);
-      const int nblk = i <= kWinMaxLog + 1 ? 1 : ((1 << (i - 1 - kColsLog)) / 4 > 0 ? (1 << (i - 1 - kColsLog)) / 4 : 1);
+      const int nblk = i <= kWinMaxLog + 1 ? 1 : pass_items(i);
       st.lvl_off[m][i] = m * kMaxLevelItems + off;
       for (int w = 0; w < nw; ++w)
         for (int b = 0; b < nblk; ++b) levels[m * kMaxLevelItems + off++] = LevelItem{m, w, b, 0};
