@@ -60,22 +60,29 @@ def workload_spec(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
-def make_input(name: str):
+def make_input(name: str, rank: int = 0):
+    """The workload's input; rank r > 0 of a multi-GPU job draws its own
+    shard of the global batch (same shapes, seed + 1000 r)."""
     from paper_1507_02525_gb300 import inputs
+    off = 1000 * rank
     if name == "single_16m":
-        return inputs.complex_signals(1, 1 << 24, seed=1).reshape(-1)
+        return inputs.complex_signals(1, 1 << 24, seed=1 + off).reshape(-1)
     if name == "single_1k":
-        return inputs.complex_signals(1, 1 << 10, seed=0).reshape(-1)
+        return inputs.complex_signals(1, 1 << 10, seed=0 + off).reshape(-1)
     if name == "single_4m":
-        return inputs.complex_signals(1, 1 << 22, seed=1).reshape(-1)
+        return inputs.complex_signals(1, 1 << 22, seed=1 + off).reshape(-1)
     if name == "tiles_4096x4k":
-        return inputs.complex_signals(4096, 1 << 12, seed=6).reshape(-1)
+        return inputs.complex_signals(4096, 1 << 12, seed=6 + off).reshape(-1)
     if name == "batch_256x64k":
-        return inputs.complex_signals(256, 1 << 16, seed=2).reshape(-1)
+        return inputs.complex_signals(256, 1 << 16, seed=2 + off).reshape(-1)
     if name == "grad_64x256k":
-        return inputs.complex_signals(64, 1 << 18, seed=4).reshape(-1)
+        return inputs.complex_signals(64, 1 << 18, seed=4 + off).reshape(-1)
     if name == "ragged_1024":
-        return inputs.ragged_real()[1]
+        lengths, samples = inputs.ragged_real()
+        if rank:  # same lengths, other samples
+            import numpy as np
+            samples = np.random.default_rng(3 + off).standard_normal(samples.size, dtype=np.float32)
+        return samples
     raise SystemExit(name)
 
 
@@ -146,6 +153,9 @@ class ClockSampler:
             return
         self.t = threading.Thread(target=self._read, daemon=True)
         self.t.start()
+        t0 = time.time()
+        while not self.lines and time.time() - t0 < 5.0 and self.proc.poll() is None:
+            time.sleep(0.05)
 
     def _read(self):
         for line in self.proc.stdout:
@@ -189,7 +199,7 @@ def oracle_sample(lengths, x_np, budget_s: float = 15.0):
     extrapolate to the whole workload.
 
     For each signal length present, level i is timed on a window-aligned slice
-    of max(2^i, 2^20) samples (the oracle's per-level cost is proportional to
+    of max(2^i, 2^22) samples (the oracle's per-level cost is proportional to
     the samples covered) and scaled to the full signal; levels are visited in
     order until the time budget is spent, later levels are extrapolated as
     proportional to i.  Returns (samples/s, cores, description)."""
@@ -212,7 +222,7 @@ def oracle_sample(lengths, x_np, budget_s: float = 15.0):
         last = None
         for i in range(1, m + 1):
             if spent < budget_s:
-                s = max(1 << i, min(n, 1 << 20))
+                s = max(1 << i, min(n, 1 << 22))
                 t0 = time.perf_counter()
                 O.forward_level(x[:s], i) if s < n else O.forward_level(x, i)
                 dt = time.perf_counter() - t0
@@ -225,7 +235,7 @@ def oracle_sample(lengths, x_np, budget_s: float = 15.0):
             total_est += per * count
     total = sum(lengths)
     desc = (f"oracle per-window FFT path (FP64, C, OpenMP); {timed_levels} (length, level) pairs timed "
-            f"on window-aligned slices of <= 2^20 samples (whole signal when a window is larger), "
+            f"on window-aligned slices of <= 2^22 samples (whole signal when a window is larger), "
             f"scaled by samples covered, remaining levels extrapolated ~ i; {spent:.1f} s of CPU time")
     return total / total_est, cores, desc
 
@@ -235,7 +245,7 @@ def oracle_sample(lengths, x_np, budget_s: float = 15.0):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="single_16m")
@@ -256,8 +266,10 @@ def main():
             return 0
         x_np = make_input(args.workload)
         vals = []
+        # every step a bounded sample, so that the whole run stays within minutes
+        per_step = max(0.5, min(4.0, 150.0 / (args.warmup + args.steps)))
         for k in range(args.warmup + args.steps):
-            v, cores, sdesc = oracle_sample(lengths, x_np, budget_s=4.0)
+            v, cores, sdesc = oracle_sample(lengths, x_np, budget_s=per_step)
             if k >= args.warmup:
                 vals.append(v)
         value = statistics.median(vals) / 1e9
@@ -274,30 +286,20 @@ def main():
         print(json.dumps(line), flush=True)
         return 0
 
-    import numpy as np
     import torch
-    from paper_1507_02525_gb300 import _lib
+    from paper_1507_02525_gb300 import _lib, replicas
 
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-
-    def barrier():
-        if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+    barrier = replicas.barrier
 
     def max_over_ranks(v: float) -> float:
-        if world == 1:
-            return v
-        import torch.distributed as dist
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(v, device=dev)
 
-    x_np = make_input(args.workload)
+    x_np = make_input(args.workload, rank)
     plan = _lib.Plan(lengths, len(lengths), real_input=real_input, graph=True)
     info = plan.info()
     xt = torch.from_numpy(x_np).to(dev)
@@ -340,12 +342,13 @@ def main():
     clk = clocks.stop()
     plan.status_poll()
 
-    # per-kernel device time (events around each launch on the launch stream)
-    plan.timing_enable(True)
+    # per-kernel device time: events around each launch, launches serialised
+    # on the bench stream so that each bracketed kernel has the GPU to itself
+    plan.timing_enable(True, serial=True)
     for _ in range(2):
         fwd()
     kf = plan.timing_read()
-    plan.timing_enable(True)
+    plan.timing_enable(True, serial=True)
     for _ in range(2):
         adj()
     ka = plan.timing_read()
@@ -353,23 +356,44 @@ def main():
 
     peak, peak_src = measured_peaks()
 
+    # a two-pass level is one unit: the cols launch writes only the plan's
+    # intermediate (no algorithmic bytes), the rows launch writes the level
+    partner = {"fwd_cols": "fwd_rows", "adj_cols": "adj_rows"}
+
     def dominant(kt, total_ms_per_step):
-        name, (ms, n, b) = max(kt.items(), key=lambda kv: kv[1][0])
+        units = {}
+        for k, (ms, n, b) in kt.items():
+            if k in partner:
+                continue
+            units[k] = [ms, n, b, [k]]
+        for k, p in partner.items():
+            if k in kt and p in units:
+                units[p][0] += kt[k][0]
+                units[p][3].insert(0 if k.endswith("cols") and p.startswith("fwd") else 1, k)
+        name, (ms, n, b, parts) = max(units.items(), key=lambda kv: kv[1][0])
         per_launch_ms = ms / n
         bytes_per_launch = b / n
         ach = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9 if bytes_per_launch else 0.0
-        traffic = ncu_traffic(name, args.workload)
+        traffic = None
+        if len(parts) == 1:
+            traffic = ncu_traffic(name, args.workload)
+        else:
+            tr = [ncu_traffic(q, args.workload) for q in parts]
+            traffic = sum(tr) if all(t is not None for t in tr) else None
         share = ms / sum(v[0] for v in kt.values())
-        return {"bound": "hbm", "kernel": f"k_{name}", "achieved": round(ach, 1), "peak": peak,
-                "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": traffic,
+        return {"bound": "hbm", "kernel": "+".join(f"k_{q}" for q in parts), "achieved": round(ach, 1),
+                "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": traffic,
                 "alg_bytes_per_launch": int(bytes_per_launch), "ms_per_launch": round(per_launch_ms, 4),
-                "share_of_step": round(share, 3), "peak_source": peak_src,
-                "per_kernel_ms": {k: round(v[0] / 2, 4) for k, v in kt.items()}}
+                "share_of_kernel_time": round(share, 3), "peak_source": peak_src,
+                "timing": "CUDA events around every launch on its stream, launches serialised, 2 steps",
+                "per_kernel_ms_per_step": {k: round(v[0] / 2, 4) for k, v in kt.items()},
+                "per_kernel_gbs": {k: round(v[2] / (v[0] * 1e-3) / 1e9, 1) for k, v in kt.items() if v[2]}}
 
     roof_fwd = dominant(kf, ms_fwd)
     roof_adj = dominant(ka, ms_adj)
-    value = world * nsamp / (ms_fwd * 1e-3) / 1e9
-    value_adj = world * nsamp / (ms_adj * 1e-3) / 1e9
+    total_samples = replicas.sum_over_ranks(nsamp, device=dev)
+    value = replicas.job_throughput(total_samples, ms_fwd) / 1e9
+    value_adj = replicas.job_throughput(total_samples, ms_adj) / 1e9
     step_frac = alg_bytes / (ms_fwd * 1e-3) / 1e9 / peak
     step_frac_adj = alg_bytes / (ms_adj * 1e-3) / 1e9 / peak
 
@@ -388,7 +412,7 @@ def main():
             plan.forward_host(xh.data_ptr(), yh.data_ptr(), s2.cuda_stream)
         dt = (time.perf_counter() - t0) / e2e_steps
         dt = max_over_ranks(dt)
-        e2e = {"value": world * nsamp / dt / 1e9, "unit": "Gsamples/s", "ms_per_step": dt * 1e3,
+        e2e = {"value": total_samples / dt / 1e9, "unit": "Gsamples/s", "ms_per_step": dt * 1e3,
                "h2d_bytes_per_step": int(xh.numel() * xh.element_size()),
                "d2h_bytes_per_step": int(yh.numel() * yh.element_size()),
                "api": "mrdft_forward_host (pinned host buffers)"}
@@ -409,7 +433,8 @@ def main():
                        "samples_per_gpu": nsamp, "alg_bytes_per_step_per_gpu": alg_bytes,
                        "l2": "inputs and outputs larger than L2 (no flush needed)" if alg_bytes > 2e8
                        else "working set smaller than L2",
-                       "parallelism": f"replicas x{world}", "graph": True,
+                       "parallelism": f"signals sharded over {world} rank(s), no collective in the path",
+                       "graph": True,
                        "kernel_source": kernel_source_hash()},
             "hbm_frac_step": round(step_frac, 4),
             "roofline": roof_fwd,

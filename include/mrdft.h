@@ -127,9 +127,9 @@ mrdft_status mrdft_plan_info(mrdft_plan_t plan, int32_t* tile_log, int32_t* fwd_
 
 /* Kernel kinds for per-kernel timing. */
 enum {
-  MRDFT_KIND_FWD_TILE = 0,   /* levels 1..12 of 4096-sample tiles */
+  MRDFT_KIND_FWD_TILE = 0,   /* levels 1..13 of 8192-sample tiles (1..m for shorter signals) */
   MRDFT_KIND_FWD_TINY = 1,   /* signals of length <= 16 */
-  MRDFT_KIND_FWD_WINDOW = 2, /* one level (13 or 14) per window */
+  MRDFT_KIND_FWD_WINDOW = 2, /* level 14, one window per CTA */
   MRDFT_KIND_FWD_COLS = 3,   /* two-pass levels, cross-chunk pass */
   MRDFT_KIND_FWD_ROWS = 4,   /* two-pass levels, per-residue pass + even bins */
   MRDFT_KIND_ADJ_TILE = 5,
@@ -143,7 +143,10 @@ enum {
 /*
  * mrdft_timing_enable -- when enable != 0, every later kernel launch of this
  * plan is bracketed by CUDA events recorded on its launch stream (graph replay
- * is bypassed meanwhile); resets the accumulated counters either way.
+ * is bypassed meanwhile); enable == 2 also issues every launch on the
+ * caller's stream, one after another, so that each bracketed launch has the
+ * GPU to itself (per-kernel rooflines); resets the accumulated counters
+ * either way.
  * mrdft_timing_read -- waits for the recorded events and returns, for one
  * kernel kind, the summed device milliseconds, the number of launches and the
  * summed algorithmic bytes of those launches (input read once plus the

@@ -150,8 +150,11 @@ class Plan:
         check(self._lib.mrdft_forward_host(self._h, ctypes.c_void_p(x_host_ptr),
                                            ctypes.c_void_p(y_host_ptr), ctypes.c_void_p(stream)), self._h)
 
-    def timing_enable(self, on: bool = True) -> None:
-        check(self._lib.mrdft_timing_enable(self._h, 1 if on else 0), self._h)
+    def timing_enable(self, on: bool = True, serial: bool = False) -> None:
+        """Bracket every launch with CUDA events; ``serial`` also runs the
+        launches one after another on the caller's stream."""
+        mode = (2 if serial else 1) if on else 0
+        check(self._lib.mrdft_timing_enable(self._h, mode), self._h)
 
     def timing_read(self) -> dict:
         """{kind: (ms, launches, algorithmic_bytes)} since timing_enable."""

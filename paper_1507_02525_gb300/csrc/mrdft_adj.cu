@@ -257,29 +257,30 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_adj_window(const AdjArgs a) 
 // =============================================================== two-pass
 
 // Adjoint of the forward two-pass level (h = Q * C, C = 2^cols_log(i)).
-// rows: item (sig, window, block) covers residues k2 in [k0, k0 + KC),
-//   KC = 2^13 / C: odd-bin gradients at k = Q k1 + k2 -> IDFT_C over k1 ->
-//   times conj(w_h^(r k2)) -> scratch U[window][k2][r]; even bins -> e_out.
-__global__ void __launch_bounds__(kRowsThreads, 1) k_adj_rows(const AdjArgs a) {
-  constexpr int NT = kRowsThreads;
-  constexpr int E = kRowsElemsLog;
+// rows: a CTA of 2^E points covers residues k2 in [k0, k0 + KC), KC = 2^E / C:
+//   odd-bin gradients at k = Q k1 + k2 -> IDFT_C over k1 -> times
+//   conj(w_h^(r k2)) -> scratch U[window][k2][r]; even bins -> e_out.
+template <int E, int NT>
+__global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_adj_rows(const AdjArgs a) {
+  constexpr int PTS = (1 << E) / NT;
   extern __shared__ __align__(1024) float2 sm[];
   float2* S = sm;                          // sequence j at j C (XOR, then pad8)
-  float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^13}
-  float2* TWL = TQ + twq_size(13);         // [KC][64] (row stride 65): w_h^(k2 t)
+  float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^E}
+  float2* TWL = TQ + twq_size(E);          // [KC][64] (row stride 65): w_h^(k2 t)
   float2* TWH = TWL + 4 * 65;              // [KC][C/64] (row stride C/64 + 1): w_h^(k2 64 u)
-  if (blockIdx.x >= a.nitems) return;
-  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  const int item = (int)blockIdx.x << (E - kPassElemsLog);
+  if (item >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
   const int i = a.level;
   const int HB = i - 1, CB = cols_log(i), QB = HB - CB;
   const int KCB = E - CB, KC = 1 << KCB;
   const int HU = (1 << CB) >> 6;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
-  const int k0 = it.block << KCB;
+  const int k0 = (it.block >> (E - kPassElemsLog)) << KCB;
   // gradient pairs (2k, 2k+1): a batch of loads is issued before any store
 #pragma unroll 1
-  for (int t0 = 0; t0 < (1 << E) / NT; t0 += 8) {
+  for (int t0 = 0; t0 < PTS; t0 += 8) {
     float4 g[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -296,7 +297,7 @@ __global__ void __launch_bounds__(kRowsThreads, 1) k_adj_rows(const AdjArgs a) {
       S[swzf((j << CB) + k1)] = make_float2(g[t].z, -g[t].w);
     }
   }
-  load_twq<NT>(TQ, 13, a.tw);
+  load_twq<NT>(TQ, E, a.tw);
   for (int t = threadIdx.x; t < KC * (64 + HU); t += NT) {
     if (t < KC * 64) {
       const int j = t >> 6, u = t & 63;
@@ -307,38 +308,39 @@ __global__ void __launch_bounds__(kRowsThreads, 1) k_adj_rows(const AdjArgs a) {
     }
   }
   __syncthreads();
-  const TwQ tw{TQ, 13};
+  const TwQ tw{TQ, E};
   float2* U = a.scratch + sd.aux_off + (w << HB);
   auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((b << CB) + n)]; };
   auto sink = [&](int, int b, int r, float2 v) MRDFT_INL {
     const float2 t = cmul(TWL[b * 65 + (r & 63)], TWH[b * (HU + 1) + (r >> 6)]);
     __stcg(U + ((int64_t)(k0 + b) << CB) + r, cmulc(conjf2(v), t));
   };
-  cg_fft<11, 13, NT, (1 << E) / NT, false, false>(S, CB, KCB, tw, src, NoPre{}, sink);
+  cg_fft<11, E, NT, PTS, false, kPreNone>(S, CB, KCB, tw, src, NoPre{}, sink);
 }
 
-// cols: item (sig, window, 2 c) covers chunk offsets r in [r0, r0 + RC),
-//   r0 = c RC, RC = 2^14 / Q: U[window][k2][r] -> IDFT_Q over k2 -> zb[r + C q]
+// cols: item (sig, window, c) covers chunk offsets r in [r0, r0 + RC),
+//   r0 = c RC, RC = 2^13 / Q: U[window][k2][r] -> IDFT_Q over k2 -> zb[r + C q]
 //   -> conj(w_{2^i}^n) zb added to acc at n and subtracted at h + n.
-__global__ void __launch_bounds__(kColsThreads, 1) k_adj_cols(const AdjArgs a) {
-  constexpr int NT = kColsThreads;
-  constexpr int E = kColsElemsLog;
+template <int NT>
+__global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
+  constexpr int E = kPassElemsLog;
+  constexpr int PTS = (1 << E) / NT;
   extern __shared__ __align__(1024) float2 sm[];
   float2* S = sm;                          // column r position k2 at k2 RC + r (XOR, then pad8)
-  float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^13}
-  float2* ZC = TQ + twq_size(13);          // w_{2^i}^(r0 + r), r < RC
-  if (2 * (int)blockIdx.x >= a.nitems) return;
-  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[2 * blockIdx.x];
+  float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^12}
+  float2* ZC = TQ + twq_size(12);          // w_{2^i}^(r0 + r), r < RC
+  if ((int)blockIdx.x >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
   const int i = a.level;
   const int HB = i - 1, CB = cols_log(i), QB = HB - CB;
   const int RCB = E - QB, RC = 1 << RCB;
   const int64_t h = (int64_t)1 << HB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
-  const int r0 = (it.block >> 1) << RCB;
+  const int r0 = it.block << RCB;
   const float2* U = a.scratch + sd.aux_off + (w << HB);
 #pragma unroll 1
-  for (int t0 = 0; t0 < (1 << E) / NT; t0 += 8) {
+  for (int t0 = 0; t0 < PTS; t0 += 8) {
     float2 u[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -348,23 +350,38 @@ __global__ void __launch_bounds__(kColsThreads, 1) k_adj_cols(const AdjArgs a) {
 #pragma unroll
     for (int t = 0; t < 8; ++t) S[swzf(threadIdx.x + (t0 + t) * NT)] = conjf2(u[t]);  // e = k2 RC + r
   }
-  load_twq<NT>(TQ, 13, a.tw);
+  load_twq<NT>(TQ, 12, a.tw);
   for (int r = threadIdx.x; r < RC; r += NT) ZC[r] = tw_any(a.tw, i, r0 + r);
   __syncthreads();
   // this block's columns of the intermediate are dead: drop them from L2
   if (RC >= 16)
     for (int l = threadIdx.x; l < (RC / 16) << QB; l += NT)
       discard_l2(U + ((int64_t)(l >> (RCB - 4)) << CB) + r0 + 16 * (l & ((RC / 16) - 1)));
-  const TwQ tw{TQ, 13};
-  const int64_t ws = w << i;
+  const TwQ tw{TQ, 12};
+  float2* acc = a.acc + sd.in_off + (w << i);
+  const bool add = sd.m > i;
   auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((n << RCB) + b)]; };
-  auto sink = [&](int, int b, int q, float2 v) MRDFT_INL {
+  float2 oa[PTS], ob[PTS];
+  // the accumulated gradient at n and h + n, read once per group of 8 outputs
+  auto pre = [&](int slot, int b, int q) MRDFT_INL {
+    if (add) {
+      const int64_t n = ((int64_t)q << CB) + r0 + b;
+      oa[slot] = __ldcg(acc + n);
+      ob[slot] = __ldcg(acc + h + n);
+    }
+  };
+  auto sink = [&](int slot, int b, int q, float2 v) MRDFT_INL {
     const int64_t n = ((int64_t)q << CB) + r0 + b;
     const float2 c = cmulc(conjf2(v), cmul(ZC[b], twq_l(tw, QB + 1, q)));
-    acc_add(a, sd, i, ws + n, c);
-    acc_add(a, sd, i, ws + h + n, make_float2(-c.x, -c.y));
+    if (add) {
+      __stcg(acc + n, cadd(oa[slot], c));
+      __stcg(acc + h + n, csub(ob[slot], c));
+    } else {
+      __stcg(acc + n, c);
+      __stcg(acc + h + n, make_float2(-c.x, -c.y));
+    }
   };
-  cg_fft<3, 12, NT, (1 << E) / NT, true, false>(S, QB, RCB, tw, src, NoPre{}, sink);
+  cg_fft<3, 11, NT, PTS, true, kPreGroup>(S, QB, RCB, tw, src, pre, sink);
 }
 
 // ================================================================ launchers
@@ -373,16 +390,23 @@ static constexpr size_t kAdjTileSmem =
     (size_t)(2 * kTile + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kAdjMaxPack * sizeof(AdjTileSig);
 static constexpr size_t kAdjWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog + 1)) * sizeof(float2);
 static constexpr size_t kAdjColsSmem =
-    (size_t)(pad8_size(1 << kColsElemsLog) + twq_size(13) + (1 << (kColsElemsLog - 3))) * sizeof(float2);
-static constexpr size_t kAdjRowsSmem =
-    (size_t)(pad8_size(1 << kRowsElemsLog) + twq_size(13) + 4 * 65 + 4 * 33) * sizeof(float2);
+    (size_t)(pad8_size(1 << kPassElemsLog) + twq_size(12) + (1 << (kPassElemsLog - 3))) * sizeof(float2);
+constexpr size_t adj_rows_smem(int E) {
+  return (size_t)(pad8_size(1 << E) + twq_size(E) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
+}
 
 cudaError_t set_adj_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_adj_tile<kTileLog, kTileThreads>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjTileSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjRowsSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjColsSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_rows<13, kPassThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)adj_rows_smem(13));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_rows<14, kPassThreadsWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)adj_rows_smem(14));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_cols<kPassThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjColsSmem);
   return e;
 }
 
@@ -399,11 +423,14 @@ cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s) {
-  k_adj_rows<<<grid, kRowsThreads, kAdjRowsSmem, s>>>(a);
+  if (rows_elems_log(a.level) == kPassElemsLog)
+    k_adj_rows<13, kPassThreads><<<grid, kPassThreads, adj_rows_smem(13), s>>>(a);
+  else
+    k_adj_rows<14, kPassThreadsWide><<<(grid + 1) / 2, kPassThreadsWide, adj_rows_smem(14), s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_adj_cols(const AdjArgs& a, int grid, cudaStream_t s) {
-  k_adj_cols<<<(grid + 1) / 2, kColsThreads, kAdjColsSmem, s>>>(a);
+  k_adj_cols<kPassThreads><<<grid, kPassThreads, kAdjColsSmem, s>>>(a);
   return cudaGetLastError();
 }
 

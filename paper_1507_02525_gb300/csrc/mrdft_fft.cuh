@@ -90,11 +90,16 @@ __device__ __forceinline__ int drev8(int v, int d) {
 //   input r of group g is w_M^((g >> SH) r) with M = L >> SH; P: pass count.
 //   FIRST: inputs come from src(b, n) in natural index n (the digit reversal
 //   is folded into the index); LAST: outputs go to sink(slot, b, k, v) with
-//   bin k natural; PRE: pre(slot, b, k) runs for every output bin before a
-//   barrier that separates every read of this pass from the sink's writes.
+//   bin k natural; PRE: pre(slot, b, k) runs for every output bin --
+//   kPreBarrier: before the barrier that separates every read of this pass
+//   from the sink's writes (the caller may read what the sink overwrites);
+//   kPreGroup: after each group's DFT, for the group's R bins, before their
+//   sinks (global reads issued in one batch per group, few registers held).
 // Every thread loads all its groups before the pass's barrier, so the pass is
 // in place; PTS bounds the points per thread (NT * PTS >= points per pass).
-template <int RB, int NT, int PTS, bool SEQ_MINOR, bool FIRST, bool LAST, bool PRE, class Src, class Pre, class Sink>
+constexpr int kPreNone = 0, kPreBarrier = 1, kPreGroup = 2;
+
+template <int RB, int NT, int PTS, bool SEQ_MINOR, bool FIRST, bool LAST, int PRE, class Src, class Pre, class Sink>
 __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq_log, int SH, int P, const TwQ& tw,
                                         Src&& src, Pre&& pre, Sink&& sink) {
   constexpr int R = 1 << RB;
@@ -132,7 +137,7 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
 #pragma unroll
         for (int r = 1; r < R; ++r) v[j][r] = cmul(v[j][r], w[r]);
       }
-      if constexpr (LAST && PRE) {
+      if constexpr (LAST && PRE == kPreBarrier) {
 #pragma unroll
         for (int k = 0; k < R; ++k) pre(j * R + k, b, g + (k << LRB));
       }
@@ -153,6 +158,10 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
     }
     dft_reg<R>(v[j]);
     if constexpr (LAST) {
+      if constexpr (PRE == kPreGroup) {
+#pragma unroll
+        for (int k = 0; k < R; ++k) pre(j * R + k, b, g + (k << LRB));
+      }
 #pragma unroll
       for (int k = 0; k < R; ++k) sink(j * R + k, b, g + (k << LRB), v[j][k]);
     } else {
@@ -167,8 +176,8 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
 // (LBMIN <= LB <= LBMAX, LB >= 1).  Starts with a barrier-free read of src,
 // ends after the sink; synchronises internally.  The caller synchronises
 // before reusing Z or reading what the sink wrote.
-//   src(b, n) -> float2;  pre(slot, b, k) (PRE only);  sink(slot, b, k, v).
-template <int LBMIN, int LBMAX, int NT, int PTS, bool SEQ_MINOR, bool PRE, class Src, class Pre, class Sink>
+//   src(b, n) -> float2;  pre(slot, b, k) (PRE != kPreNone);  sink(slot, b, k, v).
+template <int LBMIN, int LBMAX, int NT, int PTS, bool SEQ_MINOR, int PRE, class Src, class Pre, class Sink>
 __device__ __forceinline__ void cg_fft(float2* __restrict__ Z, int LB, int nseq_log, const TwQ& tw, Src&& src,
                                        Pre&& pre, Sink&& sink) {
   const int P = (LB + 2) / 3;
@@ -186,12 +195,12 @@ __device__ __forceinline__ void cg_fft(float2* __restrict__ Z, int LB, int nseq_
     static_for<1, 4>([&](auto RR) MRDFT_INL {
       constexpr int rb = decltype(RR)::value;
       if (r0 == rb)
-        cg_pass<rb, NT, PTS, SEQ_MINOR, true, false, false>(Z, LB, nseq_log, 3 * (P - 1), P, tw, src, pre, sink);
+        cg_pass<rb, NT, PTS, SEQ_MINOR, true, false, kPreNone>(Z, LB, nseq_log, 3 * (P - 1), P, tw, src, pre, sink);
     });
 #pragma unroll 1
     for (int p = P - 2; p >= 1; --p) {
       __syncthreads();
-      cg_pass<3, NT, PTS, SEQ_MINOR, false, false, false>(Z, LB, nseq_log, 3 * p, P, tw, src, pre, sink);
+      cg_pass<3, NT, PTS, SEQ_MINOR, false, false, kPreNone>(Z, LB, nseq_log, 3 * p, P, tw, src, pre, sink);
     }
     __syncthreads();
     cg_pass<3, NT, PTS, SEQ_MINOR, false, true, PRE>(Z, LB, nseq_log, 0, P, tw, src, pre, sink);
@@ -199,7 +208,7 @@ __device__ __forceinline__ void cg_fft(float2* __restrict__ Z, int LB, int nseq_
 }
 
 // Fill a quarter-wave table of w_{2^TB} in shared memory from the global
-// FP64-rounded-once table w_{2^13}^e (TB <= 13).
+// FP64-rounded-once table w_{2^14}^e (TB <= 14).
 template <int NT>
 __device__ __forceinline__ void load_twq(float2* q, int TB, const Twiddles& T) {
   const int n = 1 << (TB - 2);

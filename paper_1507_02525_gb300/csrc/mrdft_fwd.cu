@@ -282,37 +282,36 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_fwd_window(const FwdArgs a) 
 // Level i with h = 2^(i-1) = Q * C, C = 2^CB (cols_log), Q = 2^QB.
 // With n = r + C q (r < C, q < Q) and k = Q k1 + k2:
 //   DFT_h(z)[Q k1 + k2] = sum_r w_C^(r k1) w_h^(r k2) sum_q z[r + C q] w_Q^(q k2).
-// cols: item (sig, window, 2 c) covers chunk offsets r in [r0, r0 + RC),
-//   r0 = c RC, RC = 2^14 / Q: z[r + C q] -> DFT_Q over q -> scratch F[window][k2][r].
-// rows: item covers residues k2 in [k0, k0 + KC), KC = 2^13 / C:
+// cols: item (sig, window, c) covers chunk offsets r in [r0, r0 + RC),
+//   r0 = c RC, RC = 2^13 / Q: z[r + C q] -> DFT_Q over q -> scratch F[window][k2][r].
+// rows: a CTA of 2^E points covers residues k2 in [k0, k0 + KC), KC = 2^E / C:
 //   F[window][k2][.] times w_h^(r k2) -> DFT_C -> odd bin Q k1 + k2; even bin
 //   from the children; (even, odd) pairs stored at 2k.
-__global__ void __launch_bounds__(kColsThreads, 1) k_fwd_cols(const FwdArgs a) {
-  constexpr int NT = kColsThreads;
-  constexpr int E = kColsElemsLog;
+template <int NT>
+__global__ void __launch_bounds__(NT, 2) k_fwd_cols(const FwdArgs a) {
+  constexpr int E = kPassElemsLog;
+  constexpr int PTS = (1 << E) / NT;
   extern __shared__ __align__(1024) float2 sm[];
   float2* S = sm;                            // column r position q: q RC + r (XOR, then pad8)
-  float2* TQ = sm + pad8_size(1 << E);       // quarter-wave w_{2^13}
-  float2* ZC = TQ + twq_size(13);            // w_{2^i}^(r0 + r), r < RC
-  if (2 * (int)blockIdx.x >= a.nitems) return;
-  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[2 * blockIdx.x];
+  float2* TQ = sm + pad8_size(1 << E);       // quarter-wave w_{2^12}
+  float2* ZC = TQ + twq_size(12);            // w_{2^i}^(r0 + r), r < RC
+  if ((int)blockIdx.x >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
   const int i = a.level;
   const int HB = i - 1, CB = cols_log(i), QB = HB - CB;
-  const int C = 1 << CB;
   const int RCB = E - QB, RC = 1 << RCB;
   const SigDesc sd = a.sigs[it.sig];
-  const int64_t ws = (int64_t)it.window << i;
-  const int64_t xs = sd.in_off + ws;
-  const int r0 = (it.block >> 1) << RCB;
+  const int64_t xs = sd.in_off + ((int64_t)it.window << i);
+  const int r0 = it.block << RCB;
   const int64_t h = (int64_t)1 << HB;
-  load_twq<NT>(TQ, 13, a.tw);
+  load_twq<NT>(TQ, 12, a.tw);
   for (int r = threadIdx.x; r < RC; r += NT) ZC[r] = tw_any(a.tw, i, r0 + r);
   __syncthreads();
-  const TwQ tw{TQ, 13};
+  const TwQ tw{TQ, 12};
   // V (Eq. 3) and D: z[n] = (a[n] - b[n]) w_{2^i}^n, w_{2^i}^(r0 + r + C q) =
-  // w_{2^i}^(r0 + r) w_{2Q}^q; loads of a batch issued before any use
+  // w_{2^i}^(r0 + r) w_{2Q}^q; the loads of a batch are issued before any use
 #pragma unroll 1
-  for (int t0 = 0; t0 < (1 << E) / NT; t0 += 8) {
+  for (int t0 = 0; t0 < PTS; t0 += 8) {
     float2 xa[8], xb[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -332,20 +331,20 @@ __global__ void __launch_bounds__(kColsThreads, 1) k_fwd_cols(const FwdArgs a) {
   float2* F = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
   auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((n << RCB) + b)]; };
   auto sink = [&](int, int b, int k2, float2 v) MRDFT_INL { __stcg(F + ((int64_t)k2 << CB) + r0 + b, v); };
-  cg_fft<3, 12, NT, (1 << E) / NT, true, false>(S, QB, RCB, tw, src, NoPre{}, sink);
+  cg_fft<3, 11, NT, PTS, true, kPreNone>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
-__global__ void __launch_bounds__(kRowsThreads, 1) k_fwd_rows(const FwdArgs a) {
-  constexpr int NT = kRowsThreads;
-  constexpr int E = kRowsElemsLog;
+template <int E, int NT>
+__global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_fwd_rows(const FwdArgs a) {
   constexpr int PTS = (1 << E) / NT;
   extern __shared__ __align__(1024) float2 sm[];
   float2* S = sm;                          // sequence j position r at r KC + j (XOR, then pad8)
-  float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^13}
-  float2* TWL = TQ + twq_size(13);         // [KC][64] (row stride 65): w_h^(k2 t)
+  float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^E}
+  float2* TWL = TQ + twq_size(E);          // [KC][64] (row stride 65): w_h^(k2 t)
   float2* TWH = TWL + 4 * 65;              // [KC][C/64] (row stride C/64 + 1): w_h^(k2 64 u)
-  if (blockIdx.x >= a.nitems) return;
-  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  const int item = (int)blockIdx.x << (E - kPassElemsLog);
+  if (item >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
   const int i = a.level;
   const int HB = i - 1, CB = cols_log(i), QB = HB - CB;
   const int C = 1 << CB;
@@ -354,14 +353,14 @@ __global__ void __launch_bounds__(kRowsThreads, 1) k_fwd_rows(const FwdArgs a) {
   const int64_t h = (int64_t)1 << HB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t ws = (int64_t)it.window << i;
-  const int k0 = it.block << KCB;
+  const int k0 = (it.block >> (E - kPassElemsLog)) << KCB;
   const float2* F = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
 #pragma unroll 8
   for (int e = threadIdx.x; e < KC * C; e += NT) {
     const int r = e & (C - 1), j = e >> CB;
     cp_async8(S + swzf((r << KCB) + j), F + ((int64_t)(k0 + j) << CB) + r);
   }
-  load_twq<NT>(TQ, 13, a.tw);
+  load_twq<NT>(TQ, E, a.tw);
   for (int t = threadIdx.x; t < KC * (64 + HU); t += NT) {
     if (t < KC * 64) {
       const int j = t >> 6, u = t & 63;
@@ -375,27 +374,30 @@ __global__ void __launch_bounds__(kRowsThreads, 1) k_fwd_rows(const FwdArgs a) {
   __syncthreads();
   // the intermediate rows are dead now: drop them from L2 without write-back
   for (int l = threadIdx.x; l < KC * C / 16; l += NT) discard_l2(F + ((int64_t)k0 << CB) + 16 * l);
-  const TwQ tw{TQ, 13};
-  const float2* yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
+  const TwQ tw{TQ, E};
+  const float2* __restrict__ yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
   // w_h^(r k2) = w_h^(k2 (r mod 64)) w_h^(k2 64 (r / 64))
   auto src = [&](int b, int n) MRDFT_INL -> float2 {
     return cmul(S[swzf((n << KCB) + b)], cmul(TWL[b * 65 + (n & 63)], TWH[b * (HU + 1) + (n >> 6)]));
   };
   const bool reread = sd.m > i;
-  float2 ev[PTS];
+  float2 ea[PTS], eb[PTS];
+  // U (Eq. 2): the children of bin k, read once per group of 8 bins
   auto pre = [&](int slot, int b, int k1) MRDFT_INL {
     const int64_t k = ((int64_t)k1 << QB) + k0 + b;
-    ev[slot] = cadd(__ldcg(yprev + k), __ldcg(yprev + h + k));
+    ea[slot] = __ldcs(yprev + k);
+    eb[slot] = __ldcs(yprev + h + k);
   };
   auto sink = [&](int slot, int b, int k1, float2 odd) MRDFT_INL {
     const int64_t k = ((int64_t)k1 << QB) + k0 + b;
-    const float4 v = make_float4(ev[slot].x, ev[slot].y, odd.x, odd.y);
+    const float2 ev = cadd(ea[slot], eb[slot]);
+    const float4 v = make_float4(ev.x, ev.y, odd.x, odd.y);
     float4* dst = reinterpret_cast<float4*>(ycur + 2 * k);
     if (reread) __stcg(dst, v);
     else __stcs(dst, v);
   };
-  cg_fft<11, 13, NT, PTS, true, true>(S, CB, KCB, tw, src, pre, sink);
+  cg_fft<11, E, NT, PTS, true, kPreGroup>(S, CB, KCB, tw, src, pre, sink);
 }
 
 // ================================================================ launchers
@@ -405,16 +407,23 @@ static constexpr size_t kTileSmem =
 static constexpr size_t kWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog + 1)) * sizeof(float2);
 static_assert((1 << kWinMaxLog) % kWinThreads == 0, "points per thread");
 static constexpr size_t kColsSmem =
-    (size_t)(pad8_size(1 << kColsElemsLog) + twq_size(13) + (1 << (kColsElemsLog - 3))) * sizeof(float2);
-// twiddle tables: KC (64 + 1) + KC (C / 64 + 1) <= 4 * 65 + 4 * 33 for every C = 2^13 / KC >= 2^11
-static constexpr size_t kRowsSmem = (size_t)(pad8_size(1 << kRowsElemsLog) + twq_size(13) + 4 * 65 + 4 * 33) * sizeof(float2);
+    (size_t)(pad8_size(1 << kPassElemsLog) + twq_size(12) + (1 << (kPassElemsLog - 3))) * sizeof(float2);
+// twiddle tables of the rows pass: KC (64 + 1) + KC (C / 64 + 1) <= 4 * 65 + 2^(E-6) + 4
+constexpr size_t rows_smem(int E) {
+  return (size_t)(pad8_size(1 << E) + twq_size(E) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
+}
 
 cudaError_t set_fwd_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_fwd_tile<kTileLog, kTileThreads>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColsSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kRowsSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fwd_cols<kPassThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColsSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fwd_rows<13, kPassThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem(13));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fwd_rows<14, kPassThreadsWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)rows_smem(14));
   return e;
 }
 
@@ -431,11 +440,14 @@ cudaError_t launch_fwd_window(const FwdArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s) {
-  k_fwd_cols<<<(grid + 1) / 2, kColsThreads, kColsSmem, s>>>(a);
+  k_fwd_cols<kPassThreads><<<grid, kPassThreads, kColsSmem, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_rows(const FwdArgs& a, int grid, cudaStream_t s) {
-  k_fwd_rows<<<grid, kRowsThreads, kRowsSmem, s>>>(a);
+  if (rows_elems_log(a.level) == kPassElemsLog)
+    k_fwd_rows<13, kPassThreads><<<grid, kPassThreads, rows_smem(13), s>>>(a);
+  else
+    k_fwd_rows<14, kPassThreadsWide><<<(grid + 1) / 2, kPassThreadsWide, rows_smem(14), s>>>(a);
   return cudaGetLastError();
 }
 

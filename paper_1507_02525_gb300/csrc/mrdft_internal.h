@@ -42,18 +42,18 @@ constexpr int kTile = 1 << kTileLog;         // 8192 samples per tile
 constexpr int kTileThreads = 512;            // 16 samples per thread
 constexpr int kWinMaxLog = 13;               // one CTA FFT holds up to 2^13 points
 constexpr int kWinThreads = 512;
-// two-pass levels (i >= 15): h = Q * C with C = 2^cols_log(i); the cols pass
-// holds 2^14 points per CTA, the rows pass 2^13 (2 CTAs per SM)
-constexpr int kColsLog = 11;
-constexpr int kColsElemsLog = 14;
-constexpr int kRowsElemsLog = 13;
-constexpr int kColsThreads = 512;
-constexpr int kRowsThreads = 512;
-// log2 C for level i: 2^11 up to level 24, then growing so that Q <= 2^12
-__host__ __device__ constexpr int cols_log(int i) { return (i - 1) - 12 > kColsLog ? (i - 1) - 12 : kColsLog; }
-// work items of a two-pass level, per window: one per rows CTA (2^(i-14));
-// the cols pass takes every other item (2^(i-15) CTAs per window)
-__host__ __device__ constexpr int pass_items(int i) { return 1 << ((i - 1) - kRowsElemsLog); }
+// Two-pass levels (i >= 15), h = 2^(i-1) = Q * C with C = 2^cols_log(i):
+// 2^11 up to level 23, then 2^(i-12) so that Q <= 2^11.
+//   cols pass: 2^13 points per CTA (RC = 2^13 / Q chunk offsets), 2 CTAs/SM
+//   rows pass: 2^rows_elems_log(i) points per CTA (KC = 2^E / C residues)
+constexpr int kPassElemsLog = 13;
+constexpr int kPassThreads = 256;        // 2^13-point CTAs: 32 points per thread
+constexpr int kPassThreadsWide = 512;    // the 2^14-point rows CTA (level 26)
+__host__ __device__ constexpr int cols_log(int i) { return (i - 1) - 11 > 11 ? (i - 1) - 11 : 11; }
+__host__ __device__ constexpr int rows_elems_log(int i) { return cols_log(i) > 13 ? cols_log(i) : 13; }
+// work items of a two-pass level, per window: one per cols CTA (2^(i-14));
+// a rows CTA of 2^E points takes every 2^(E-13)-th item
+__host__ __device__ constexpr int pass_items(int i) { return 1 << ((i - 1) - kPassElemsLog); }
 
 struct FwdArgs {
   const void* x;  // float2* (complex64) or float* (real FP32)

@@ -94,7 +94,7 @@ struct mrdft_plan_s {
   LevelItem* d_levels = nullptr;
   std::vector<Segment> segments;
   std::vector<Launch> top;  // levels above seg_log, ascending, whole plan
-  int seg_log = 20;
+  int seg_log = 22;
   int nstreams = 4;
   std::vector<cudaStream_t> workers;
   std::vector<cudaEvent_t> ev_join;
@@ -114,8 +114,11 @@ struct mrdft_plan_s {
   std::map<GraphKey, cudaGraphExec_t> fwd_graphs, adj_graphs;
   std::string err = "no error";
 
-  // optional per-kernel timing (events around every launch, no graph replay)
+  // optional per-kernel timing (events around every launch, no graph replay);
+  // timing_serial also runs the segments one after another on the caller's
+  // stream, so that every bracketed launch has the GPU to itself
   bool timing = false;
+  bool timing_serial = false;
   struct Pending {
     int kind;
     cudaEvent_t a, b;
@@ -444,7 +447,7 @@ mrdft_status launch_fwd(mrdft_plan_s* p, FwdArgs a, const Launch& L, cudaStream_
 // caller's stream, which also works under stream capture).
 template <class F>
 mrdft_status run_segments(mrdft_plan_s* p, cudaStream_t st, F&& chain) {
-  const int nw = (int)p->workers.size();
+  const int nw = p->timing_serial ? 0 : (int)p->workers.size();
   if (nw <= 1) {
     for (size_t j = 0; j < p->segments.size(); ++j) {
       mrdft_status r = chain(p->segments[j], st);
@@ -705,6 +708,7 @@ mrdft_status mrdft_timing_enable(mrdft_plan_t p, int enable) {
   if (!p) return fail(nullptr, MRDFT_EINVAL, "mrdft_timing_enable: plan is NULL");
   collect_timing(p);
   p->timing = enable != 0;
+  p->timing_serial = enable == 2;
   for (int k = 0; k < MRDFT_KIND_COUNT; ++k) {
     p->t_ms[k] = 0.0;
     p->t_launches[k] = 0;
