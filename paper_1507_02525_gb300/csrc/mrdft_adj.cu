@@ -254,15 +254,23 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_adj_window(const AdjArgs a) 
   cg_fft<kTileLog, kWinMaxLog, NT, (1 << kWinMaxLog) / NT, false, false>(Z, LB, 0, tw, src, NoPre{}, sink);
 }
 
+static constexpr size_t kAdjColsSmem =
+    (size_t)(pad8_size(1 << kPassElemsLog) + twq_size(12) + (1 << (kPassElemsLog - 3))) * sizeof(float2);
+constexpr size_t adj_rows_smem(int E) {
+  return (size_t)(pad8_size(1 << E) + twq_size(E) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
+}
+
 // =============================================================== two-pass
 
 // Adjoint of the forward two-pass level (h = Q * C, C = 2^cols_log(i)).
 // rows: a CTA of 2^E points covers residues k2 in [k0, k0 + KC), KC = 2^E / C:
 //   odd-bin gradients at k = Q k1 + k2 -> IDFT_C over k1 -> times
 //   conj(w_h^(r k2)) -> scratch U[window][k2][r]; even bins -> e_out.
-template <int E, int NT>
+template <int E, int NT, int CB>
 __global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_adj_rows(const AdjArgs a) {
   constexpr int PTS = (1 << E) / NT;
+  constexpr int KCB = E - CB, KC = 1 << KCB;
+  constexpr int HU = (1 << CB) >> 6;
   extern __shared__ __align__(1024) float2 sm[];
   float2* S = sm;                          // sequence j at j C (XOR, then pad8)
   float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^E}
@@ -272,9 +280,7 @@ __global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_adj_rows(con
   if (item >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
   const int i = a.level;
-  const int HB = i - 1, CB = cols_log(i), QB = HB - CB;
-  const int KCB = E - CB, KC = 1 << KCB;
-  const int HU = (1 << CB) >> 6;
+  const int HB = i - 1, QB = HB - CB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
   const int k0 = (it.block >> (E - kPassElemsLog)) << KCB;
@@ -315,16 +321,17 @@ __global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_adj_rows(con
     const float2 t = cmul(TWL[b * 65 + (r & 63)], TWH[b * (HU + 1) + (r >> 6)]);
     __stcg(U + ((int64_t)(k0 + b) << CB) + r, cmulc(conjf2(v), t));
   };
-  cg_fft<11, E, NT, PTS, false, kPreNone>(S, CB, KCB, tw, src, NoPre{}, sink);
+  cg_fft<CB, CB, NT, PTS, false, kPreNone>(S, CB, KCB, tw, src, NoPre{}, sink);
 }
 
 // cols: item (sig, window, c) covers chunk offsets r in [r0, r0 + RC),
 //   r0 = c RC, RC = 2^13 / Q: U[window][k2][r] -> IDFT_Q over k2 -> zb[r + C q]
 //   -> conj(w_{2^i}^n) zb added to acc at n and subtracted at h + n.
-template <int NT>
+template <int NT, int QB>
 __global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
   constexpr int E = kPassElemsLog;
   constexpr int PTS = (1 << E) / NT;
+  constexpr int RCB = E - QB, RC = 1 << RCB;
   extern __shared__ __align__(1024) float2 sm[];
   float2* S = sm;                          // column r position k2 at k2 RC + r (XOR, then pad8)
   float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^12}
@@ -332,8 +339,7 @@ __global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
   if ((int)blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
   const int i = a.level;
-  const int HB = i - 1, CB = cols_log(i), QB = HB - CB;
-  const int RCB = E - QB, RC = 1 << RCB;
+  const int HB = i - 1, CB = HB - QB;
   const int64_t h = (int64_t)1 << HB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
@@ -381,7 +387,31 @@ __global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
       __stcg(acc + h + n, make_float2(-c.x, -c.y));
     }
   };
-  cg_fft<3, 11, NT, PTS, true, kPreGroup>(S, QB, RCB, tw, src, pre, sink);
+  cg_fft<QB, QB, NT, PTS, true, kPreGroup>(S, QB, RCB, tw, src, pre, sink);
+}
+
+// Launch-time dispatch to the instantiation of a level's FFT sizes.
+template <int QB>
+void adj_cols_launch(const AdjArgs& a, int grid, cudaStream_t s) {
+  k_adj_cols<kPassThreads, QB><<<grid, kPassThreads, kAdjColsSmem, s>>>(a);
+}
+template <int CB>
+void adj_rows_launch(const AdjArgs& a, int grid, cudaStream_t s) {
+  constexpr int E = CB > kPassElemsLog ? CB : kPassElemsLog;
+  constexpr int NT = E == kPassElemsLog ? kPassThreads : kPassThreadsWide;
+  k_adj_rows<E, NT, CB><<<grid >> (E - kPassElemsLog), NT, adj_rows_smem(E), s>>>(a);
+}
+template <int QB>
+cudaError_t adj_cols_attr() {
+  return cudaFuncSetAttribute(k_adj_cols<kPassThreads, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kAdjColsSmem);
+}
+template <int CB>
+cudaError_t adj_rows_attr() {
+  constexpr int E = CB > kPassElemsLog ? CB : kPassElemsLog;
+  constexpr int NT = E == kPassElemsLog ? kPassThreads : kPassThreadsWide;
+  return cudaFuncSetAttribute(k_adj_rows<E, NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)adj_rows_smem(E));
 }
 
 // ================================================================ launchers
@@ -389,24 +419,16 @@ __global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
 static constexpr size_t kAdjTileSmem =
     (size_t)(2 * kTile + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kAdjMaxPack * sizeof(AdjTileSig);
 static constexpr size_t kAdjWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog + 1)) * sizeof(float2);
-static constexpr size_t kAdjColsSmem =
-    (size_t)(pad8_size(1 << kPassElemsLog) + twq_size(12) + (1 << (kPassElemsLog - 3))) * sizeof(float2);
-constexpr size_t adj_rows_smem(int E) {
-  return (size_t)(pad8_size(1 << E) + twq_size(E) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
-}
-
 cudaError_t set_adj_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_adj_tile<kTileLog, kTileThreads>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjTileSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adj_rows<13, kPassThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)adj_rows_smem(13));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adj_rows<14, kPassThreadsWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)adj_rows_smem(14));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adj_cols<kPassThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjColsSmem);
+  static_for_host<3, 12>([&](auto Q) {
+    if (e == cudaSuccess) e = adj_cols_attr<decltype(Q)::value>();
+  });
+  static_for_host<11, 15>([&](auto C) {
+    if (e == cudaSuccess) e = adj_rows_attr<decltype(C)::value>();
+  });
   return e;
 }
 
@@ -423,14 +445,17 @@ cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s) {
-  if (rows_elems_log(a.level) == kPassElemsLog)
-    k_adj_rows<13, kPassThreads><<<grid, kPassThreads, adj_rows_smem(13), s>>>(a);
-  else
-    k_adj_rows<14, kPassThreadsWide><<<(grid + 1) / 2, kPassThreadsWide, adj_rows_smem(14), s>>>(a);
+  const int CB = cols_log(a.level);
+  static_for_host<11, 15>([&](auto C) {
+    if (CB == decltype(C)::value) adj_rows_launch<decltype(C)::value>(a, grid, s);
+  });
   return cudaGetLastError();
 }
 cudaError_t launch_adj_cols(const AdjArgs& a, int grid, cudaStream_t s) {
-  k_adj_cols<kPassThreads><<<grid, kPassThreads, kAdjColsSmem, s>>>(a);
+  const int QB = (a.level - 1) - cols_log(a.level);
+  static_for_host<3, 12>([&](auto Q) {
+    if (QB == decltype(Q)::value) adj_cols_launch<decltype(Q)::value>(a, grid, s);
+  });
   return cudaGetLastError();
 }
 

@@ -75,6 +75,15 @@ __device__ __forceinline__ void static_for(F&& f) {
   }
 }
 
+// host-side compile-time loop (launch dispatch over template instantiations)
+template <int B, int E, typename F>
+inline void static_for_host(F&& f) {
+  if constexpr (B < E) {
+    f(IC<B>{});
+    static_for_host<B + 1, E>(f);
+  }
+}
+
 __host__ __device__ constexpr int ilog2c(int v) { return v <= 1 ? 0 : 1 + ilog2c(v >> 1); }
 __host__ __device__ constexpr int bitrevc(int v, int bits) {
   int r = 0;

@@ -277,6 +277,13 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_fwd_window(const FwdArgs a) 
   cg_fft<kTileLog, kWinMaxLog, NT, PTS, false, true>(Z, LB, 0, tw, src, pre, sink);
 }
 
+static constexpr size_t kColsSmem =
+    (size_t)(pad8_size(1 << kPassElemsLog) + twq_size(12) + (1 << (kPassElemsLog - 3))) * sizeof(float2);
+// twiddle tables of the rows pass: KC (64 + 1) + KC (C / 64 + 1) <= 4 * 65 + 2^(E-6) + 4
+constexpr size_t rows_smem(int E) {
+  return (size_t)(pad8_size(1 << E) + twq_size(E) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
+}
+
 // =============================================================== two-pass
 
 // Level i with h = 2^(i-1) = Q * C, C = 2^CB (cols_log), Q = 2^QB.
@@ -287,10 +294,11 @@ __global__ void __launch_bounds__(kWinThreads, 1) k_fwd_window(const FwdArgs a) 
 // rows: a CTA of 2^E points covers residues k2 in [k0, k0 + KC), KC = 2^E / C:
 //   F[window][k2][.] times w_h^(r k2) -> DFT_C -> odd bin Q k1 + k2; even bin
 //   from the children; (even, odd) pairs stored at 2k.
-template <int NT>
+template <int NT, int QB>
 __global__ void __launch_bounds__(NT, 2) k_fwd_cols(const FwdArgs a) {
   constexpr int E = kPassElemsLog;
   constexpr int PTS = (1 << E) / NT;
+  constexpr int RCB = E - QB, RC = 1 << RCB;
   extern __shared__ __align__(1024) float2 sm[];
   float2* S = sm;                            // column r position q: q RC + r (XOR, then pad8)
   float2* TQ = sm + pad8_size(1 << E);       // quarter-wave w_{2^12}
@@ -298,8 +306,7 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(const FwdArgs a) {
   if ((int)blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
   const int i = a.level;
-  const int HB = i - 1, CB = cols_log(i), QB = HB - CB;
-  const int RCB = E - QB, RC = 1 << RCB;
+  const int HB = i - 1, CB = HB - QB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t xs = sd.in_off + ((int64_t)it.window << i);
   const int r0 = it.block << RCB;
@@ -331,12 +338,15 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(const FwdArgs a) {
   float2* F = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
   auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((n << RCB) + b)]; };
   auto sink = [&](int, int b, int k2, float2 v) MRDFT_INL { __stcg(F + ((int64_t)k2 << CB) + r0 + b, v); };
-  cg_fft<3, 11, NT, PTS, true, kPreNone>(S, QB, RCB, tw, src, NoPre{}, sink);
+  cg_fft<QB, QB, NT, PTS, true, kPreNone>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
-template <int E, int NT>
+template <int E, int NT, int CB>
 __global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_fwd_rows(const FwdArgs a) {
   constexpr int PTS = (1 << E) / NT;
+  constexpr int C = 1 << CB;
+  constexpr int KCB = E - CB, KC = 1 << KCB;
+  constexpr int HU = C >> 6;               // rows of the high twiddle table
   extern __shared__ __align__(1024) float2 sm[];
   float2* S = sm;                          // sequence j position r at r KC + j (XOR, then pad8)
   float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^E}
@@ -346,10 +356,7 @@ __global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_fwd_rows(con
   if (item >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
   const int i = a.level;
-  const int HB = i - 1, CB = cols_log(i), QB = HB - CB;
-  const int C = 1 << CB;
-  const int KCB = E - CB, KC = 1 << KCB;
-  const int HU = C >> 6;                   // rows of the high twiddle table
+  const int HB = i - 1, QB = HB - CB;
   const int64_t h = (int64_t)1 << HB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t ws = (int64_t)it.window << i;
@@ -397,7 +404,30 @@ __global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_fwd_rows(con
     if (reread) __stcg(dst, v);
     else __stcs(dst, v);
   };
-  cg_fft<11, E, NT, PTS, true, kPreGroup>(S, CB, KCB, tw, src, pre, sink);
+  cg_fft<CB, CB, NT, PTS, true, kPreGroup>(S, CB, KCB, tw, src, pre, sink);
+}
+
+// Launch-time dispatch to the instantiation of a level's FFT sizes.
+template <int QB>
+void cols_launch(const FwdArgs& a, int grid, cudaStream_t s) {
+  k_fwd_cols<kPassThreads, QB><<<grid, kPassThreads, kColsSmem, s>>>(a);
+}
+template <int CB>
+void rows_launch(const FwdArgs& a, int grid, cudaStream_t s) {
+  constexpr int E = CB > kPassElemsLog ? CB : kPassElemsLog;
+  constexpr int NT = E == kPassElemsLog ? kPassThreads : kPassThreadsWide;
+  k_fwd_rows<E, NT, CB><<<grid >> (E - kPassElemsLog), NT, rows_smem(E), s>>>(a);
+}
+template <int QB>
+cudaError_t cols_attr() {
+  return cudaFuncSetAttribute(k_fwd_cols<kPassThreads, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)kColsSmem);
+}
+template <int CB>
+cudaError_t rows_attr() {
+  constexpr int E = CB > kPassElemsLog ? CB : kPassElemsLog;
+  constexpr int NT = E == kPassElemsLog ? kPassThreads : kPassThreadsWide;
+  return cudaFuncSetAttribute(k_fwd_rows<E, NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem(E));
 }
 
 // ================================================================ launchers
@@ -406,24 +436,16 @@ static constexpr size_t kTileSmem =
     (size_t)(kTile + pad16_size(kTile) + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kMaxPack * sizeof(TileSig);
 static constexpr size_t kWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog + 1)) * sizeof(float2);
 static_assert((1 << kWinMaxLog) % kWinThreads == 0, "points per thread");
-static constexpr size_t kColsSmem =
-    (size_t)(pad8_size(1 << kPassElemsLog) + twq_size(12) + (1 << (kPassElemsLog - 3))) * sizeof(float2);
-// twiddle tables of the rows pass: KC (64 + 1) + KC (C / 64 + 1) <= 4 * 65 + 2^(E-6) + 4
-constexpr size_t rows_smem(int E) {
-  return (size_t)(pad8_size(1 << E) + twq_size(E) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
-}
-
 cudaError_t set_fwd_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_fwd_tile<kTileLog, kTileThreads>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_fwd_cols<kPassThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kColsSmem);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_fwd_rows<13, kPassThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem(13));
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_fwd_rows<14, kPassThreadsWide>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)rows_smem(14));
+  static_for_host<3, 12>([&](auto Q) {
+    if (e == cudaSuccess) e = cols_attr<decltype(Q)::value>();
+  });
+  static_for_host<11, 15>([&](auto C) {
+    if (e == cudaSuccess) e = rows_attr<decltype(C)::value>();
+  });
   return e;
 }
 
@@ -440,14 +462,17 @@ cudaError_t launch_fwd_window(const FwdArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s) {
-  k_fwd_cols<kPassThreads><<<grid, kPassThreads, kColsSmem, s>>>(a);
+  const int QB = (a.level - 1) - cols_log(a.level);
+  static_for_host<3, 12>([&](auto Q) {
+    if (QB == decltype(Q)::value) cols_launch<decltype(Q)::value>(a, grid, s);
+  });
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_rows(const FwdArgs& a, int grid, cudaStream_t s) {
-  if (rows_elems_log(a.level) == kPassElemsLog)
-    k_fwd_rows<13, kPassThreads><<<grid, kPassThreads, rows_smem(13), s>>>(a);
-  else
-    k_fwd_rows<14, kPassThreadsWide><<<(grid + 1) / 2, kPassThreadsWide, rows_smem(14), s>>>(a);
+  const int CB = cols_log(a.level);
+  static_for_host<11, 15>([&](auto C) {
+    if (CB == decltype(C)::value) rows_launch<decltype(C)::value>(a, grid, s);
+  });
   return cudaGetLastError();
 }
 
