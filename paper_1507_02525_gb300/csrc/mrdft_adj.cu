@@ -124,9 +124,11 @@ __global__ void __launch_bounds__(NT, 1) k_adj_tile(const AdjArgs a) {
 
   // ---- levels tl .. 5 through shared memory
   const TwQ tw{TQ, TLOG};
-#pragma unroll 1
-  for (int i = tl; i >= 5; --i) {
-    const int L = 1 << i, h = L >> 1;
+  // one specialised FFT per level (compile-time lengths), top level first
+  static_for<0, TLOG - 4>([&](auto J) MRDFT_INL {
+    constexpr int i = TLOG - decltype(J)::value;
+    if (i > tl) return;
+    constexpr int L = 1 << i, h = L >> 1;
     const float2* Ein = E[(i + 1) & 1];
     float2* Eout = E[i & 1];
     // G_i = g_i + P_i: even half -> Eout, conj(odd half) -> Z
@@ -158,9 +160,9 @@ __global__ void __launch_bounds__(NT, 1) k_adj_tile(const AdjArgs a) {
       ACC[i0] = cadd(ACC[i0], c);
       ACC[i1] = csub(ACC[i1], c);
     };
-    cg_fft<4, TLOG - 1, NT, 8, false, false>(Z, i - 1, tn_log - i, tw, src, NoPre{}, sink);
+    cg_fft<i - 1, i - 1, NT, 8, false, false>(Z, i - 1, tn_log - i, tw, src, NoPre{}, sink);
     __syncthreads();
-  }
+  });
 
   // ---- levels 4 .. 1 in registers, one 16-position chunk per thread
   {

@@ -25,9 +25,10 @@ namespace mrdft {
 
 __device__ __forceinline__ int pad8(int a) { return a + (a >> 3); }
 __host__ __device__ constexpr int pad8_size(int n) { return n + n / 8; }
-// one pad element per 16 (level buffers: lane-consecutive and window-strided
-// 8-byte accesses stay conflict-free, and (2k, 2k+1) stay adjacent)
-__device__ __forceinline__ int pad16(int a) { return a + (a >> 4); }
+// two pad elements per 32 (level buffers: lane-consecutive 8-byte reads and
+// window-strided accesses stay conflict-free, and every pair (2k, 2k+1) stays
+// adjacent and 16-byte aligned, so a bin pair moves as one 16-byte access)
+__device__ __forceinline__ int pad16(int a) { return a + ((a >> 5) << 1); }
 __host__ __device__ constexpr int pad16_size(int n) { return n + n / 16; }
 
 // Twiddles w_{2^TB}^e from a quarter-wave table q[r] = w_{2^TB}^r, r < 2^(TB-2)

@@ -105,7 +105,8 @@ __device__ __forceinline__ void tile_chunk_levels_1_4(const FwdArgs& a, const fl
       __stcs(dst + q, make_float4(yr[2 * q].x, yr[2 * q].y, yr[2 * q + 1].x, yr[2 * q + 1].y));
   });
 #pragma unroll
-  for (int q = 0; q < 16; ++q) B4[pad16((chunk << 4) + q)] = yr[q];
+  for (int q = 0; q < 8; ++q)
+    st4s(B4 + pad16((chunk << 4) + 2 * q), make_float4(yr[2 * q].x, yr[2 * q].y, yr[2 * q + 1].x, yr[2 * q + 1].y));
 }
 
 template <int TLOG, int NT>
@@ -162,9 +163,11 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tile(const FwdArgs a) {
   // place: every child read (pre) happens before the barrier in the last pass
   const TwQ tw{TQ, TLOG};
   const bool single = it.nsig == 1;
-#pragma unroll 1
-  for (int i = 5; i <= tl; ++i) {
-    const int h = 1 << (i - 1);
+  // one specialised FFT per level (compile-time lengths)
+  static_for<5, TLOG + 1>([&](auto I) MRDFT_INL {
+    constexpr int i = decltype(I)::value;
+    if (i > tl) return;
+    constexpr int h = 1 << (i - 1);
     const bool keep = i < tl;  // the next level reads this one
     float2* ylev = a.y + TS[0].out_base + ((int64_t)(i - 1) << TS[0].m);  // single-signal tile
     const bool l2keep = i == tl && TS[0].m > tl;  // re-read as children of level tl+1
@@ -180,11 +183,7 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tile(const FwdArgs a) {
     auto sink = [&](int slot, int b, int k, float2 odd) MRDFT_INL {
       const int e = (b << i) + 2 * k;
       const float4 v = make_float4(ev[slot].x, ev[slot].y, odd.x, odd.y);
-      if (keep) {
-        const int pe = pad16(e);
-        B[pe] = ev[slot];
-        B[pe + 1] = odd;
-      }
+      if (keep) st4s(B + pad16(e), v);
       float4* dst;
       if (single) {
         dst = reinterpret_cast<float4*>(ylev + e);
@@ -195,9 +194,9 @@ __global__ void __launch_bounds__(NT, 1) k_fwd_tile(const FwdArgs a) {
       if (l2keep) __stcg(dst, v);
       else __stcs(dst, v);
     };
-    cg_fft<4, TLOG - 1, NT, 8, false, true>(Z, i - 1, tn_log - i, tw, src, pre, sink);
+    cg_fft<i - 1, i - 1, NT, 8, false, true>(Z, i - 1, tn_log - i, tw, src, pre, sink);
     __syncthreads();
-  }
+  });
 }
 
 // ===================================================================== tiny
