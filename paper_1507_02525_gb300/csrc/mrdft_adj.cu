@@ -87,7 +87,7 @@ __device__ __forceinline__ void adj_chunk_levels_4_1(const AdjArgs& a, const Adj
 }
 
 template <int TLOG, int NT>
-__global__ void __launch_bounds__(NT, 1) k_adj_tile(const AdjArgs a) {
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArgs a) {
   constexpr int T = 1 << TLOG;
   static_assert(T == 16 * NT, "tile = 16 samples per thread");
   extern __shared__ __align__(1024) float2 sm[];

@@ -110,7 +110,7 @@ __device__ __forceinline__ void tile_chunk_levels_1_4(const FwdArgs& a, const fl
 }
 
 template <int TLOG, int NT>
-__global__ void __launch_bounds__(NT, 1) k_fwd_tile(const FwdArgs a) {
+__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArgs a) {
   constexpr int T = 1 << TLOG;
   static_assert(T == 16 * NT, "tile = 16 samples per thread");
   extern __shared__ __align__(1024) float2 sm[];

@@ -37,9 +37,9 @@ struct LevelItem {
   int32_t pad;
 };
 
-constexpr int kTileLog = 13;                 // in-tile levels 1..13
-constexpr int kTile = 1 << kTileLog;         // 8192 samples per tile
-constexpr int kTileThreads = 512;            // 16 samples per thread
+constexpr int kTileLog = 12;                 // in-tile levels 1..12
+constexpr int kTile = 1 << kTileLog;         // 4096 samples per tile
+constexpr int kTileThreads = 256;            // 16 samples per thread, 2 CTAs per SM
 constexpr int kWinMaxLog = 13;               // one CTA FFT holds up to 2^13 points
 constexpr int kWinThreads = 512;
 // Two-pass levels (i >= 15), h = 2^(i-1) = Q * C with C = 2^cols_log(i):
