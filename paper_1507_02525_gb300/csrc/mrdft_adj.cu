@@ -114,6 +114,14 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
   const SigDesc sd0 = a.sigs[a.sig_ids[it.sig_list]];
   const bool below = sd0.m > tl;
   __syncthreads();
+  // every level reads its gradient slice once, in a latency-bound burst: keep
+  // the next two levels' slices on their way into L2 (one bulk request per signal)
+  auto prefetch_level = [&](int lv) MRDFT_INL {
+    if (lv >= 1 && tid < it.nsig)
+      prefetch_l2_bulk(a.gy + TS[tid].g_base + ((int64_t)(lv - 1) << TS[tid].m), (uint32_t)(sizeof(float2) << tl));
+  };
+  prefetch_level(tl);
+  prefetch_level(tl - 1);
 #pragma unroll 4
   for (int c = tid; c < (Tn >> 1); c += NT) {
     const int e = c << 1;
@@ -129,6 +137,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     constexpr int i = TLOG - decltype(J)::value;
     if (i > tl) return;
     constexpr int L = 1 << i, h = L >> 1;
+    prefetch_level(i - 2);
+    if constexpr (i == 5) {  // levels 2 and 1 follow level 3 in registers
+      prefetch_level(2);
+      prefetch_level(1);
+    }
     const float2* Ein = E[(i + 1) & 1];
     float2* Eout = E[i & 1];
     // G_i = g_i + P_i: even half -> Eout, conj(odd half) -> Z
@@ -217,43 +230,69 @@ __device__ __forceinline__ float4 adj_G(const AdjArgs& a, const SigDesc& sd, int
   return g;
 }
 
-__device__ __forceinline__ void acc_add(const AdjArgs& a, const SigDesc& sd, int i, int64_t idx, float2 c) {
-  float2* p = a.acc + sd.in_off + idx;
-  if (sd.m > i) {
-    float2 o = __ldcg(p);
-    c = cadd(o, c);
-  }
-  __stcg(p, c);
-}
-
-__global__ void __launch_bounds__(kWinThreads, 1) k_adj_window(const AdjArgs a) {
+// One window of level i = LB + 1 per CTA: G = g + propagated even bins; even
+// half -> e_out; IDFT_h of the odd half; conj(w_{2^i}^n) times it added to
+// the accumulator at n and subtracted at h + n (accumulator read per group).
+template <int LB>
+__global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) {
   constexpr int NT = kWinThreads;
+  constexpr int h = 1 << LB;
+  constexpr int i = LB + 1;
+  constexpr int PTS = h / NT;
   extern __shared__ __align__(1024) float2 sm[];
   float2* Z = sm;                               // pad8
-  float2* TQ = sm + pad8_size(1 << kWinMaxLog);
-  if (blockIdx.x >= a.nitems) return;
+  float2* TQ = sm + pad8_size(1 << kWinMaxLog); // quarter-wave w_{2^13}
+  if ((int)blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
-  const int i = a.level;
-  const int LB = i - 1;
-  const int h = 1 << LB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
-  load_twq<NT>(TQ, kWinMaxLog + 1, a.tw);
-  for (int k = threadIdx.x; k < h; k += NT) {
-    const float4 g = adj_G(a, sd, i, w, 2 * (int64_t)k);
-    __stcg(a.e_out + sd.aux_off + (w << LB) + k, make_float2(g.x, g.y));
-    Z[swzf(k)] = make_float2(g.z, -g.w);
+  const bool add = sd.m > i;
+  float2* acc = a.acc + sd.in_off + (w << i);
+  // the accumulator is read only after the FFT: start moving it into L2 now
+  if (add && threadIdx.x < 2 * (h / 2048))
+    prefetch_l2_bulk(acc + (threadIdx.x >> 1) * 2048 + (threadIdx.x & 1) * h, 2048 * sizeof(float2));
+  load_twq<NT>(TQ, 13, a.tw);
+  const float2 w1 = __ldg(&a.tw.tw13[1]);  // w_{2^14}
+#pragma unroll 1
+  for (int t0 = 0; t0 < PTS; t0 += 8) {
+    float4 g[8];
+#pragma unroll
+    for (int t = 0; t < 8; ++t) g[t] = adj_G(a, sd, i, w, 2 * (int64_t)(threadIdx.x + (t0 + t) * NT));
+#pragma unroll
+    for (int t = 0; t < 8; ++t) {
+      const int k = threadIdx.x + (t0 + t) * NT;
+      __stcg(a.e_out + sd.aux_off + (w << LB) + k, make_float2(g[t].x, g[t].y));
+      Z[swzf(k)] = make_float2(g[t].z, -g[t].w);
+    }
   }
   __syncthreads();
-  const TwQ tw{TQ, kWinMaxLog + 1};
-  const int64_t ws = w << i;
+  const TwQ tw{TQ, 13};
   auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[swzf(n)]; };
-  auto sink = [&](int, int, int n, float2 v) MRDFT_INL {
-    const float2 c = cmulc(conjf2(v), twq_l(tw, i, n));
-    acc_add(a, sd, i, ws + n, c);
-    acc_add(a, sd, i, ws + h + n, make_float2(-c.x, -c.y));
+  float2 oa[PTS], ob[PTS];
+  auto pre = [&](int slot, int, int n) MRDFT_INL {
+    if (add) {
+      oa[slot] = __ldcg(acc + n);
+      ob[slot] = __ldcg(acc + h + n);
+    }
   };
-  cg_fft<kTileLog, kWinMaxLog, NT, (1 << kWinMaxLog) / NT, false, false>(Z, LB, 0, tw, src, NoPre{}, sink);
+  auto sink = [&](int slot, int, int n, float2 v) MRDFT_INL {
+    float2 t;
+    if constexpr (i <= 13) {
+      t = twq_l(tw, i, n);
+    } else {
+      t = twq(tw, n >> 1);
+      if (n & 1) t = cmul(t, w1);
+    }
+    const float2 c = cmulc(conjf2(v), t);  // conj(w^n) zb[n]
+    if (add) {
+      __stcg(acc + n, cadd(oa[slot], c));
+      __stcg(acc + h + n, csub(ob[slot], c));
+    } else {
+      __stcg(acc + n, c);
+      __stcg(acc + h + n, make_float2(-c.x, -c.y));
+    }
+  };
+  cg_fft<LB, LB, NT, PTS, false, kPreGroup>(Z, LB, 0, tw, src, pre, sink);
 }
 
 static constexpr size_t kAdjColsSmem =
@@ -347,6 +386,8 @@ __global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
   const int64_t w = it.window;
   const int r0 = it.block << RCB;
   const float2* U = a.scratch + sd.aux_off + (w << HB);
+  float2* acc = a.acc + sd.in_off + (w << i);
+  const bool add = sd.m > i;
 #pragma unroll 1
   for (int t0 = 0; t0 < PTS; t0 += 8) {
     float2 u[8];
@@ -366,8 +407,6 @@ __global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
     for (int l = threadIdx.x; l < (RC / 16) << QB; l += NT)
       discard_l2(U + ((int64_t)(l >> (RCB - 4)) << CB) + r0 + 16 * (l & ((RC / 16) - 1)));
   const TwQ tw{TQ, 12};
-  float2* acc = a.acc + sd.in_off + (w << i);
-  const bool add = sd.m > i;
   auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((n << RCB) + b)]; };
   float2 oa[PTS], ob[PTS];
   // the accumulated gradient at n and h + n, read once per group of 8 outputs
@@ -420,11 +459,14 @@ cudaError_t adj_rows_attr() {
 
 static constexpr size_t kAdjTileSmem =
     (size_t)(2 * kTile + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kAdjMaxPack * sizeof(AdjTileSig);
-static constexpr size_t kAdjWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog + 1)) * sizeof(float2);
+static constexpr size_t kAdjWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(13)) * sizeof(float2);
 cudaError_t set_adj_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_adj_tile<kTileLog, kTileThreads>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjTileSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_adj_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_window<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_window<13>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
   static_for_host<3, 12>([&](auto Q) {
     if (e == cudaSuccess) e = adj_cols_attr<decltype(Q)::value>();
   });
@@ -443,7 +485,10 @@ cudaError_t launch_adj_tiny(const AdjArgs& a, int nsig_tiny, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s) {
-  k_adj_window<<<grid, kWinThreads, kAdjWinSmem, s>>>(a);
+  if (a.level == 13)
+    k_adj_window<12><<<grid, kWinThreads, kAdjWinSmem, s>>>(a);
+  else
+    k_adj_window<13><<<grid, kWinThreads, kAdjWinSmem, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s) {

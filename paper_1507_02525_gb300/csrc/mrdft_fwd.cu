@@ -220,60 +220,74 @@ __global__ void k_fwd_tiny(const FwdArgs a) {
 
 // =================================================================== window
 
-// One window of level i (h = 2^(i-1) <= 2^13 odd-bin DFT points) per CTA:
+// One window of level i = LB + 1 (h = 2^LB odd-bin DFT points) per CTA:
 // z from x, DFT_h in shared memory, even bins from the level-(i-1) children
-// in y (prefetched into registers before the last pass), (even, odd) pairs
-// stored at 2k.
-__global__ void __launch_bounds__(kWinThreads, 1) k_fwd_window(const FwdArgs a) {
+// in y (moved into L2 when the CTA starts, read per group of 8 bins), (even,
+// odd) pairs stored at 2k.
+template <int LB>
+__global__ void __launch_bounds__(kWinThreads, 2) k_fwd_window(const FwdArgs a) {
   constexpr int NT = kWinThreads;
-  constexpr int PTS = (1 << kWinMaxLog) / NT;   // points per thread per pass
+  constexpr int h = 1 << LB;
+  constexpr int i = LB + 1;
+  constexpr int PTS = h / NT;                   // points per thread per pass
   extern __shared__ __align__(1024) float2 sm[];
-  float2* Z = sm;                               // 2^13 (pad8; XOR layout while staging)
-  float2* TQ = sm + pad8_size(1 << kWinMaxLog); // quarter-wave w_{2^14}
-  if (blockIdx.x >= a.nitems) return;
+  float2* Z = sm;                               // 2^LB (pad8; XOR layout while staging)
+  float2* TQ = sm + pad8_size(1 << kWinMaxLog); // quarter-wave w_{2^13}
+  if ((int)blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
-  const int i = a.level;
-  const int LB = i - 1;
-  const int h = 1 << LB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t ws = (int64_t)it.window << i;
   const int64_t xs = sd.in_off + ws;
   const float2* yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
-  load_twq<NT>(TQ, kWinMaxLog + 1, a.tw);
+  // the children are read only after the FFT: start moving them into L2 now
+  if (threadIdx.x < 2 * (h / 2048))
+    prefetch_l2_bulk(yprev + (threadIdx.x >> 1) * 2048 + (threadIdx.x & 1) * h, 2048 * sizeof(float2));
+  load_twq<NT>(TQ, 13, a.tw);
+  // w_{2^14}^n = w_{2^13}^(n/2) w_{2^14}^(n mod 2)
+  const float2 w1 = __ldg(&a.tw.tw13[1]);
   __syncthreads();
-  const TwQ tw{TQ, kWinMaxLog + 1};
-  // V (Eq. 3) and D: z[n] = (a[n] - b[n]) w_{2^i}^n; all loads of a thread are
-  // issued before any use, then z is staged in the XOR layout that the first
-  // FFT pass reads in digit-reversed order
-  {
-    float2 xa[PTS], xb[PTS];
+  const TwQ tw{TQ, 13};
+  // V (Eq. 3) and D: z[n] = (a[n] - b[n]) w_{2^i}^n, loads issued 8 at a time,
+  // z staged in the XOR layout that the first FFT pass reads digit-reversed
+#pragma unroll 1
+  for (int t0 = 0; t0 < PTS; t0 += 8) {
+    float2 xa[8], xb[8];
 #pragma unroll
-    for (int q = 0; q < PTS; ++q) {
-      const int n = threadIdx.x + q * NT;
-      if (n < h) {
-        xa[q] = load_x1(a, xs + n);
-        xb[q] = load_x1(a, xs + h + n);
-      }
+    for (int t = 0; t < 8; ++t) {
+      const int n = threadIdx.x + (t0 + t) * NT;
+      xa[t] = load_x1(a, xs + n);
+      xb[t] = load_x1(a, xs + h + n);
     }
 #pragma unroll
-    for (int q = 0; q < PTS; ++q) {
-      const int n = threadIdx.x + q * NT;
-      if (n < h) Z[swzf(n)] = cmul(csub(xa[q], xb[q]), twq_l(tw, i, n));
+    for (int t = 0; t < 8; ++t) {
+      const int n = threadIdx.x + (t0 + t) * NT;
+      float2 w;
+      if constexpr (i <= 13) {
+        w = twq_l(tw, i, n);
+      } else {
+        w = twq(tw, n >> 1);
+        if (n & 1) w = cmul(w, w1);
+      }
+      Z[swzf(n)] = cmul(csub(xa[t], xb[t]), w);
     }
   }
   __syncthreads();
   const bool reread = sd.m > i;  // children of the next level: keep in L2
-  float2 ev[PTS];
+  float2 ea[PTS], eb[PTS];
   auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[swzf(n)]; };
-  auto pre = [&](int slot, int, int k) MRDFT_INL { ev[slot] = cadd(__ldcg(yprev + k), __ldcg(yprev + h + k)); };
+  auto pre = [&](int slot, int, int k) MRDFT_INL {
+    ea[slot] = __ldcs(yprev + k);
+    eb[slot] = __ldcs(yprev + h + k);
+  };
   auto sink = [&](int slot, int, int k, float2 odd) MRDFT_INL {
-    const float4 v = make_float4(ev[slot].x, ev[slot].y, odd.x, odd.y);
+    const float2 ev = cadd(ea[slot], eb[slot]);
+    const float4 v = make_float4(ev.x, ev.y, odd.x, odd.y);
     float4* dst = reinterpret_cast<float4*>(ycur + 2 * k);
     if (reread) __stcg(dst, v);
     else __stcs(dst, v);
   };
-  cg_fft<kTileLog, kWinMaxLog, NT, PTS, false, true>(Z, LB, 0, tw, src, pre, sink);
+  cg_fft<LB, LB, NT, PTS, false, kPreGroup>(Z, LB, 0, tw, src, pre, sink);
 }
 
 static constexpr size_t kColsSmem =
@@ -310,6 +324,10 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(const FwdArgs a) {
   const int64_t xs = sd.in_off + ((int64_t)it.window << i);
   const int r0 = it.block << RCB;
   const int64_t h = (int64_t)1 << HB;
+  // x rows r0 .. r0 + RC of every chunk q, both halves: start moving them into
+  // L2 (the loads below come in batches)
+  for (int q = threadIdx.x; q < 2 << QB; q += NT) prefetch_l2(reinterpret_cast<const char*>(a.x) +
+      (xs + (int64_t)(q >> 1) * (1 << CB) + (q & 1) * h + r0) * (a.in_real ? 4 : 8));
   load_twq<NT>(TQ, 12, a.tw);
   for (int r = threadIdx.x; r < RC; r += NT) ZC[r] = tw_any(a.tw, i, r0 + r);
   __syncthreads();
@@ -361,6 +379,7 @@ __global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_fwd_rows(con
   const int64_t ws = (int64_t)it.window << i;
   const int k0 = (it.block >> (E - kPassElemsLog)) << KCB;
   const float2* F = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
+  const float2* __restrict__ yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
 #pragma unroll 8
   for (int e = threadIdx.x; e < KC * C; e += NT) {
     const int r = e & (C - 1), j = e >> CB;
@@ -381,7 +400,6 @@ __global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_fwd_rows(con
   // the intermediate rows are dead now: drop them from L2 without write-back
   for (int l = threadIdx.x; l < KC * C / 16; l += NT) discard_l2(F + ((int64_t)k0 << CB) + 16 * l);
   const TwQ tw{TQ, E};
-  const float2* __restrict__ yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
   // w_h^(r k2) = w_h^(k2 (r mod 64)) w_h^(k2 64 (r / 64))
   auto src = [&](int b, int n) MRDFT_INL -> float2 {
@@ -433,12 +451,15 @@ cudaError_t rows_attr() {
 
 static constexpr size_t kTileSmem =
     (size_t)(kTile + pad16_size(kTile) + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kMaxPack * sizeof(TileSig);
-static constexpr size_t kWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(kWinMaxLog + 1)) * sizeof(float2);
+static constexpr size_t kWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(13)) * sizeof(float2);
 static_assert((1 << kWinMaxLog) % kWinThreads == 0, "points per thread");
 cudaError_t set_fwd_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_fwd_tile<kTileLog, kTileThreads>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_window, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fwd_window<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fwd_window<13>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmem);
   static_for_host<3, 12>([&](auto Q) {
     if (e == cudaSuccess) e = cols_attr<decltype(Q)::value>();
   });
@@ -457,7 +478,10 @@ cudaError_t launch_fwd_tiny(const FwdArgs& a, int nsig_tiny, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_window(const FwdArgs& a, int grid, cudaStream_t s) {
-  k_fwd_window<<<grid, kWinThreads, kWinSmem, s>>>(a);
+  if (a.level == 13)
+    k_fwd_window<12><<<grid, kWinThreads, kWinSmem, s>>>(a);
+  else
+    k_fwd_window<13><<<grid, kWinThreads, kWinSmem, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s) {

@@ -41,7 +41,7 @@ constexpr int kTileLog = 12;                 // in-tile levels 1..12
 constexpr int kTile = 1 << kTileLog;         // 4096 samples per tile
 constexpr int kTileThreads = 256;            // 16 samples per thread, 2 CTAs per SM
 constexpr int kWinMaxLog = 13;               // one CTA FFT holds up to 2^13 points
-constexpr int kWinThreads = 512;
+constexpr int kWinThreads = 256;             // levels 13, 14: 16 or 32 points per thread
 // Two-pass levels (i >= 15), h = 2^(i-1) = Q * C with C = 2^cols_log(i):
 // 2^11 up to level 23, then 2^(i-12) so that Q <= 2^11.
 //   cols pass: 2^13 points per CTA (RC = 2^13 / Q chunk offsets), 2 CTAs/SM
