@@ -93,8 +93,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
   extern __shared__ __align__(1024) float2 sm[];
   float2* ACC = sm;                        // T, x_bar accumulator (swz128)
   float2* E[2] = {sm + T, sm + T + T / 2}; // even-bin propagation, level i in E[i & 1]
-  float2* Z = sm + 2 * T;                  // T/2 (pad8), odd-bin inverse DFT work
-  float2* TQ = Z + pad8_size(T / 2);       // quarter-wave w_{2^TLOG} (padded)
+  float2* Z = sm + 2 * T;                  // T/2 (staging, then zlay), odd-bin inverse DFT work
+  float2* TQ = Z + T / 2;                  // quarter-wave w_{2^TLOG} (padded)
   AdjTileSig* TS = reinterpret_cast<AdjTileSig*>(TQ + twq_size(TLOG));
   const int tid = threadIdx.x;
   const int item = blockIdx.x;
@@ -137,6 +137,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     constexpr int i = TLOG - decltype(J)::value;
     if (i > tl) return;
     constexpr int L = 1 << i, h = L >> 1;
+    constexpr int SA = i <= 10 ? 3 : 6;  // staging layout of the odd half
     prefetch_level(i - 2);
     if constexpr (i == 5) {  // levels 2 and 1 follow level 3 in registers
       prefetch_level(2);
@@ -162,10 +163,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
         p = make_float4(pe.x, pe.y, po.x, po.y);
       }
       Eout[swzf(w * h + (k >> 1))] = make_float2(g.x + p.x, g.y + p.y);
-      Z[swzf(w * h + (k >> 1))] = make_float2(g.z + p.z, -(g.w + p.w));
+      Z[stg<SA, 0>(w * h + (k >> 1))] = make_float2(g.z + p.z, -(g.w + p.w));
     }
     __syncthreads();
-    auto src = [&](int b, int n) MRDFT_INL -> float2 { return Z[swzf((b << (i - 1)) + n)]; };
+    auto src = [&](int b, int n) MRDFT_INL -> float2 { return Z[stg<SA, 0>((b << (i - 1)) + n)]; };
     auto sink = [&](int, int b, int n, float2 v) MRDFT_INL {
       const float2 c = cmulc(conjf2(v), twq_l(tw, i, n));  // conj(w^n) zb[n]
       const int base = b << i;
@@ -239,9 +240,10 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) 
   constexpr int h = 1 << LB;
   constexpr int i = LB + 1;
   constexpr int PTS = h / NT;
+  constexpr int SA = LB == 12 ? 6 : 3, SB = LB == 12 ? 0 : 9;  // staging layout
   extern __shared__ __align__(1024) float2 sm[];
-  float2* Z = sm;                               // pad8
-  float2* TQ = sm + pad8_size(1 << kWinMaxLog); // quarter-wave w_{2^13}
+  float2* Z = sm;                               // staging layout, then zlay
+  float2* TQ = sm + (1 << kWinMaxLog);          // quarter-wave w_{2^13}
   if ((int)blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
   const SigDesc sd = a.sigs[it.sig];
@@ -262,12 +264,12 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) 
     for (int t = 0; t < 8; ++t) {
       const int k = threadIdx.x + (t0 + t) * NT;
       __stcg(a.e_out + sd.aux_off + (w << LB) + k, make_float2(g[t].x, g[t].y));
-      Z[swzf(k)] = make_float2(g[t].z, -g[t].w);
+      Z[stg<SA, SB>(k)] = make_float2(g[t].z, -g[t].w);
     }
   }
   __syncthreads();
   const TwQ tw{TQ, 13};
-  auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[swzf(n)]; };
+  auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[stg<SA, SB>(n)]; };
   float2 oa[PTS], ob[PTS];
   auto pre = [&](int slot, int, int n) MRDFT_INL {
     if (add) {
@@ -296,10 +298,12 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) 
 }
 
 static constexpr size_t kAdjColsSmem =
-    (size_t)(pad8_size(1 << kPassElemsLog) + twq_size(12) + (1 << (kPassElemsLog - 3))) * sizeof(float2);
-constexpr size_t adj_rows_smem(int E) {
-  return (size_t)(pad8_size(1 << E) + twq_size(E) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
+    (size_t)((1 << kPassElemsLog) + twq_size(12) + (1 << (kPassElemsLog - 3))) * sizeof(float2);
+constexpr size_t adj_rows_smem(int E, int CB) {
+  return (size_t)((1 << E) + twq_size(CB) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
 }
+template <int CB>
+constexpr int adj_rows_e() { return rows_elems_log_c(CB); }
 
 // =============================================================== two-pass
 
@@ -308,23 +312,36 @@ constexpr size_t adj_rows_smem(int E) {
 //   odd-bin gradients at k = Q k1 + k2 -> IDFT_C over k1 -> times
 //   conj(w_h^(r k2)) -> scratch U[window][k2][r]; even bins -> e_out.
 template <int E, int NT, int CB>
-__global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_adj_rows(const AdjArgs a) {
+__global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(const AdjArgs a) {
   constexpr int PTS = (1 << E) / NT;
   constexpr int KCB = E - CB, KC = 1 << KCB;
   constexpr int HU = (1 << CB) >> 6;
+  constexpr int SH = E - kPassElemsLog;    // CTAs per item: 2^-SH (SH < 0), items per CTA: 2^SH
+  // staging layout
+  constexpr int SA = CB <= 10 ? 5 : (CB <= 12 ? 6 : 3), SB = CB <= 10 ? 8 : 9;
   extern __shared__ __align__(1024) float2 sm[];
-  float2* S = sm;                          // sequence j at j C (XOR, then pad8)
-  float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^E}
-  float2* TWL = TQ + twq_size(E);          // [KC][64] (row stride 65): w_h^(k2 t)
+  float2* S = sm;                          // sequence j at j C (staging, then zlay)
+  float2* TQ = sm + (1 << E);              // quarter-wave w_C
+  float2* TWL = TQ + twq_size(CB);         // [KC][64] (row stride 65): w_h^(k2 t)
   float2* TWH = TWL + 4 * 65;              // [KC][C/64] (row stride C/64 + 1): w_h^(k2 64 u)
-  const int item = (int)blockIdx.x << (E - kPassElemsLog);
+  int item, blk;
+  if constexpr (SH >= 0) {
+    item = (int)blockIdx.x << SH;
+  } else {
+    item = (int)blockIdx.x >> -SH;
+  }
   if (item >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
+  if constexpr (SH >= 0) {
+    blk = it.block >> SH;
+  } else {
+    blk = (it.block << -SH) | ((int)blockIdx.x & ((1 << -SH) - 1));
+  }
   const int i = a.level;
   const int HB = i - 1, QB = HB - CB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
-  const int k0 = (it.block >> (E - kPassElemsLog)) << KCB;
+  const int k0 = blk << KCB;
   // gradient pairs (2k, 2k+1): a batch of loads is issued before any store
 #pragma unroll 1
   for (int t0 = 0; t0 < PTS; t0 += 8) {
@@ -341,10 +358,10 @@ __global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_adj_rows(con
       const int j = e & (KC - 1), k1 = e >> KCB;
       const int64_t k = ((int64_t)k1 << QB) + k0 + j;
       __stcg(a.e_out + sd.aux_off + (w << HB) + k, make_float2(g[t].x, g[t].y));
-      S[swzf((j << CB) + k1)] = make_float2(g[t].z, -g[t].w);
+      S[stg<SA, SB>((j << CB) + k1)] = make_float2(g[t].z, -g[t].w);
     }
   }
-  load_twq<NT>(TQ, E, a.tw);
+  load_twq<NT>(TQ, CB, a.tw);
   for (int t = threadIdx.x; t < KC * (64 + HU); t += NT) {
     if (t < KC * 64) {
       const int j = t >> 6, u = t & 63;
@@ -355,9 +372,9 @@ __global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_adj_rows(con
     }
   }
   __syncthreads();
-  const TwQ tw{TQ, E};
+  const TwQ tw{TQ, CB};
   float2* U = a.scratch + sd.aux_off + (w << HB);
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((b << CB) + n)]; };
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[stg<SA, SB>((b << CB) + n)]; };
   auto sink = [&](int, int b, int r, float2 v) MRDFT_INL {
     const float2 t = cmul(TWL[b * 65 + (r & 63)], TWH[b * (HU + 1) + (r >> 6)]);
     __stcg(U + ((int64_t)(k0 + b) << CB) + r, cmulc(conjf2(v), t));
@@ -374,8 +391,8 @@ __global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
   constexpr int PTS = (1 << E) / NT;
   constexpr int RCB = E - QB, RC = 1 << RCB;
   extern __shared__ __align__(1024) float2 sm[];
-  float2* S = sm;                          // column r position k2 at k2 RC + r (XOR, then pad8)
-  float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^12}
+  float2* S = sm;                          // column r position k2 at k2 RC + r (staging, then zlay)
+  float2* TQ = sm + (1 << E);              // quarter-wave w_{2^12}
   float2* ZC = TQ + twq_size(12);          // w_{2^i}^(r0 + r), r < RC
   if ((int)blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
@@ -397,7 +414,7 @@ __global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
       u[t] = __ldcg(U + ((int64_t)(e >> RCB) << CB) + r0 + (e & (RC - 1)));
     }
 #pragma unroll
-    for (int t = 0; t < 8; ++t) S[swzf(threadIdx.x + (t0 + t) * NT)] = conjf2(u[t]);  // e = k2 RC + r
+    for (int t = 0; t < 8; ++t) S[stg<6, 0>(threadIdx.x + (t0 + t) * NT)] = conjf2(u[t]);  // e = k2 RC + r
   }
   load_twq<NT>(TQ, 12, a.tw);
   for (int r = threadIdx.x; r < RC; r += NT) ZC[r] = tw_any(a.tw, i, r0 + r);
@@ -407,7 +424,7 @@ __global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
     for (int l = threadIdx.x; l < (RC / 16) << QB; l += NT)
       discard_l2(U + ((int64_t)(l >> (RCB - 4)) << CB) + r0 + 16 * (l & ((RC / 16) - 1)));
   const TwQ tw{TQ, 12};
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((n << RCB) + b)]; };
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[stg<6, 0>((n << RCB) + b)]; };
   float2 oa[PTS], ob[PTS];
   // the accumulated gradient at n and h + n, read once per group of 8 outputs
   auto pre = [&](int slot, int b, int q) MRDFT_INL {
@@ -428,7 +445,7 @@ __global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
       __stcg(acc + h + n, make_float2(-c.x, -c.y));
     }
   };
-  cg_fft<QB, QB, NT, PTS, true, kPreGroup>(S, QB, RCB, tw, src, pre, sink);
+  cg_fft<QB, QB, NT, PTS, true, kPreGroup, (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, pre, sink);
 }
 
 // Launch-time dispatch to the instantiation of a level's FFT sizes.
@@ -438,9 +455,9 @@ void adj_cols_launch(const AdjArgs& a, int grid, cudaStream_t s) {
 }
 template <int CB>
 void adj_rows_launch(const AdjArgs& a, int grid, cudaStream_t s) {
-  constexpr int E = CB > kPassElemsLog ? CB : kPassElemsLog;
-  constexpr int NT = E == kPassElemsLog ? kPassThreads : kPassThreadsWide;
-  k_adj_rows<E, NT, CB><<<grid >> (E - kPassElemsLog), NT, adj_rows_smem(E), s>>>(a);
+  constexpr int E = adj_rows_e<CB>();
+  constexpr int NT = E <= kPassElemsLog ? kPassThreads : kPassThreadsWide;
+  k_adj_rows<E, NT, CB><<<rows_grid(a.level, true, grid), NT, adj_rows_smem(E, CB), s>>>(a);
 }
 template <int QB>
 cudaError_t adj_cols_attr() {
@@ -449,17 +466,17 @@ cudaError_t adj_cols_attr() {
 }
 template <int CB>
 cudaError_t adj_rows_attr() {
-  constexpr int E = CB > kPassElemsLog ? CB : kPassElemsLog;
-  constexpr int NT = E == kPassElemsLog ? kPassThreads : kPassThreadsWide;
+  constexpr int E = adj_rows_e<CB>();
+  constexpr int NT = E <= kPassElemsLog ? kPassThreads : kPassThreadsWide;
   return cudaFuncSetAttribute(k_adj_rows<E, NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)adj_rows_smem(E));
+                              (int)adj_rows_smem(E, CB));
 }
 
 // ================================================================ launchers
 
 static constexpr size_t kAdjTileSmem =
-    (size_t)(2 * kTile + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kAdjMaxPack * sizeof(AdjTileSig);
-static constexpr size_t kAdjWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(13)) * sizeof(float2);
+    (size_t)(2 * kTile + kTile / 2 + twq_size(kTileLog)) * sizeof(float2) + kAdjMaxPack * sizeof(AdjTileSig);
+static constexpr size_t kAdjWinSmem = (size_t)((1 << kWinMaxLog) + twq_size(13)) * sizeof(float2);
 cudaError_t set_adj_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_adj_tile<kTileLog, kTileThreads>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjTileSmem);
@@ -467,10 +484,10 @@ cudaError_t set_adj_attributes() {
     e = cudaFuncSetAttribute(k_adj_window<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_adj_window<13>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
-  static_for_host<3, 12>([&](auto Q) {
+  static_for_host<4, 12>([&](auto Q) {
     if (e == cudaSuccess) e = adj_cols_attr<decltype(Q)::value>();
   });
-  static_for_host<11, 15>([&](auto C) {
+  static_for_host<10, 15>([&](auto C) {
     if (e == cudaSuccess) e = adj_rows_attr<decltype(C)::value>();
   });
   return e;
@@ -492,15 +509,15 @@ cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s) {
-  const int CB = cols_log(a.level);
-  static_for_host<11, 15>([&](auto C) {
+  const int CB = cols_log(a.level, true);
+  static_for_host<10, 15>([&](auto C) {
     if (CB == decltype(C)::value) adj_rows_launch<decltype(C)::value>(a, grid, s);
   });
   return cudaGetLastError();
 }
 cudaError_t launch_adj_cols(const AdjArgs& a, int grid, cudaStream_t s) {
-  const int QB = (a.level - 1) - cols_log(a.level);
-  static_for_host<3, 12>([&](auto Q) {
+  const int QB = (a.level - 1) - cols_log(a.level, true);
+  static_for_host<4, 12>([&](auto Q) {
     if (QB == decltype(Q)::value) adj_cols_launch<decltype(Q)::value>(a, grid, s);
   });
   return cudaGetLastError();

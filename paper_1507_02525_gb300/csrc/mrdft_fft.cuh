@@ -9,13 +9,16 @@
 // so the last pass emits bins in natural order with consecutive lanes on
 // consecutive bins.  All radices are 8 except the first pass (2, 4 or 8).
 //
-// Shared layout: element a of the work buffer lives at pad8(a) = a + a/8, so
-// both the 8-consecutive reads and the lane-consecutive strided writes are
-// free of bank conflicts and their addresses are a base plus constants.  The
-// first pass reads its input through src(); callers that stage the input in
-// shared memory use the XOR layout swzf() there, which absorbs the
-// digit-reversed (power-of-two strided) read pattern; the first pass then
-// rewrites the buffer in place in the pad8 layout.
+// Shared layout (no padding): element a of the work buffer lives at
+// zlay<ZS>(a), an XOR permutation inside every aligned block of 16 elements
+// chosen so that, for 8-byte accesses, every half-warp of a pass touches 16
+// distinct bank pairs both when it reads 8 consecutive elements per lane and
+// when it writes lane-consecutive elements; ZS = log2 of the number of
+// interleaved sequences for position-major storage (capped at 4), 0 for
+// sequence-major storage.  The first pass reads its input through src();
+// callers that stage the input in shared memory use an XOR layout stg<A,B>()
+// there, picked per FFT shape so that the digit-reversed read of the first
+// pass is conflict-free; the first pass then rewrites the buffer in place.
 // Sequences are stored sequence-major (b * L + pos) or, SEQ_MINOR,
 // position-major (pos * nseq + b, consecutive lanes on consecutive sequences).
 #pragma once
@@ -24,6 +27,17 @@
 namespace mrdft {
 
 __device__ __forceinline__ int pad8(int a) { return a + (a >> 3); }
+template <int ZS>
+__device__ __forceinline__ int zlay(int a) {
+  if constexpr (ZS >= 4) return a;
+  else return a ^ (((a >> (3 + ZS)) & ((1 << (4 - ZS)) - 1)) << ZS);
+}
+// staging layout: the low 4 index bits XOR bits A.. (and B.., B > 0)
+template <int A, int B>
+__device__ __forceinline__ int stg(int e) {
+  if constexpr (B == 0) return e ^ ((e >> A) & 15);
+  else return e ^ (((e >> A) ^ (e >> B)) & 15);
+}
 __host__ __device__ constexpr int pad8_size(int n) { return n + n / 8; }
 // two pad elements per 32 (level buffers: lane-consecutive 8-byte reads and
 // window-strided accesses stay conflict-free, and every pair (2k, 2k+1) stays
@@ -100,7 +114,7 @@ __device__ __forceinline__ int drev8(int v, int d) {
 // in place; PTS bounds the points per thread (NT * PTS >= points per pass).
 constexpr int kPreNone = 0, kPreBarrier = 1, kPreGroup = 2;
 
-template <int RB, int NT, int PTS, bool SEQ_MINOR, bool FIRST, bool LAST, int PRE, class Src, class Pre, class Sink>
+template <int RB, int NT, int PTS, bool SEQ_MINOR, bool FIRST, bool LAST, int PRE, int ZS, class Src, class Pre, class Sink>
 __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq_log, int SH, int P, const TwQ& tw,
                                         Src&& src, Pre&& pre, Sink&& sink) {
   constexpr int R = 1 << RB;
@@ -129,7 +143,7 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
       } else {
         const int a0 = SEQ_MINOR ? (((g << RB) << nseq_log) + b) : ((b << LB) + (g << RB));
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[j][r] = Z[pad8(a0 + (SEQ_MINOR ? (r << nseq_log) : r))];
+        for (int r = 0; r < R; ++r) v[j][r] = Z[zlay<ZS>(a0 + (SEQ_MINOR ? (r << nseq_log) : r))];
       }
       const int tg = g >> SH;
       if (tg != 0) {
@@ -168,7 +182,7 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
     } else {
       const int a0 = SEQ_MINOR ? ((g << nseq_log) + b) : ((b << LB) + g);
 #pragma unroll
-      for (int k = 0; k < R; ++k) Z[pad8(a0 + (SEQ_MINOR ? ((k << LRB) << nseq_log) : (k << LRB)))] = v[j][k];
+      for (int k = 0; k < R; ++k) Z[zlay<ZS>(a0 + (SEQ_MINOR ? ((k << LRB) << nseq_log) : (k << LRB)))] = v[j][k];
     }
   }
 }
@@ -178,7 +192,7 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
 // ends after the sink; synchronises internally.  The caller synchronises
 // before reusing Z or reading what the sink wrote.
 //   src(b, n) -> float2;  pre(slot, b, k) (PRE != kPreNone);  sink(slot, b, k, v).
-template <int LBMIN, int LBMAX, int NT, int PTS, bool SEQ_MINOR, int PRE, class Src, class Pre, class Sink>
+template <int LBMIN, int LBMAX, int NT, int PTS, bool SEQ_MINOR, int PRE, int ZS = 0, class Src, class Pre, class Sink>
 __device__ __forceinline__ void cg_fft(float2* __restrict__ Z, int LB, int nseq_log, const TwQ& tw, Src&& src,
                                        Pre&& pre, Sink&& sink) {
   const int P = (LB + 2) / 3;
@@ -188,7 +202,7 @@ __device__ __forceinline__ void cg_fft(float2* __restrict__ Z, int LB, int nseq_
       constexpr int rb = decltype(RR)::value;
       if constexpr (rb >= LBMIN && rb <= LBMAX)
         if (r0 == rb)
-          cg_pass<rb, NT, PTS, SEQ_MINOR, true, true, PRE>(Z, LB, nseq_log, LB, 1, tw, src, pre, sink);
+          cg_pass<rb, NT, PTS, SEQ_MINOR, true, true, PRE, ZS>(Z, LB, nseq_log, LB, 1, tw, src, pre, sink);
     });
     return;
   }
@@ -196,15 +210,15 @@ __device__ __forceinline__ void cg_fft(float2* __restrict__ Z, int LB, int nseq_
     static_for<1, 4>([&](auto RR) MRDFT_INL {
       constexpr int rb = decltype(RR)::value;
       if (r0 == rb)
-        cg_pass<rb, NT, PTS, SEQ_MINOR, true, false, kPreNone>(Z, LB, nseq_log, 3 * (P - 1), P, tw, src, pre, sink);
+        cg_pass<rb, NT, PTS, SEQ_MINOR, true, false, kPreNone, ZS>(Z, LB, nseq_log, 3 * (P - 1), P, tw, src, pre, sink);
     });
 #pragma unroll 1
     for (int p = P - 2; p >= 1; --p) {
       __syncthreads();
-      cg_pass<3, NT, PTS, SEQ_MINOR, false, false, kPreNone>(Z, LB, nseq_log, 3 * p, P, tw, src, pre, sink);
+      cg_pass<3, NT, PTS, SEQ_MINOR, false, false, kPreNone, ZS>(Z, LB, nseq_log, 3 * p, P, tw, src, pre, sink);
     }
     __syncthreads();
-    cg_pass<3, NT, PTS, SEQ_MINOR, false, true, PRE>(Z, LB, nseq_log, 0, P, tw, src, pre, sink);
+    cg_pass<3, NT, PTS, SEQ_MINOR, false, true, PRE, ZS>(Z, LB, nseq_log, 0, P, tw, src, pre, sink);
   }
 }
 

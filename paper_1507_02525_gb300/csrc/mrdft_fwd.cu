@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
   extern __shared__ __align__(1024) float2 sm[];
   float2* X = sm;                       // x tile (swz128)
   float2* B = sm + T;                   // current level, updated in place (pad16)
-  float2* Z = B + pad16_size(T);        // odd-bin DFT work area (pad8)
-  float2* TQ = Z + pad8_size(T / 2);    // quarter-wave w_{2^TLOG} (padded)
+  float2* Z = B + pad16_size(T);        // odd-bin DFT work area (zlay)
+  float2* TQ = Z + T / 2;               // quarter-wave w_{2^TLOG} (padded)
   TileSig* TS = reinterpret_cast<TileSig*>(TQ + twq_size(TLOG));
   const int tid = threadIdx.x;
   const int item = blockIdx.x;
@@ -230,9 +230,10 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_fwd_window(const FwdArgs a) 
   constexpr int h = 1 << LB;
   constexpr int i = LB + 1;
   constexpr int PTS = h / NT;                   // points per thread per pass
+  constexpr int SA = LB == 12 ? 6 : 3, SB = LB == 12 ? 0 : 9;  // staging layout
   extern __shared__ __align__(1024) float2 sm[];
-  float2* Z = sm;                               // 2^LB (pad8; XOR layout while staging)
-  float2* TQ = sm + pad8_size(1 << kWinMaxLog); // quarter-wave w_{2^13}
+  float2* Z = sm;                               // 2^LB (staging layout, then zlay)
+  float2* TQ = sm + (1 << kWinMaxLog);          // quarter-wave w_{2^13}
   if ((int)blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
   const SigDesc sd = a.sigs[it.sig];
@@ -269,13 +270,13 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_fwd_window(const FwdArgs a) 
         w = twq(tw, n >> 1);
         if (n & 1) w = cmul(w, w1);
       }
-      Z[swzf(n)] = cmul(csub(xa[t], xb[t]), w);
+      Z[stg<SA, SB>(n)] = cmul(csub(xa[t], xb[t]), w);
     }
   }
   __syncthreads();
   const bool reread = sd.m > i;  // children of the next level: keep in L2
   float2 ea[PTS], eb[PTS];
-  auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[swzf(n)]; };
+  auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[stg<SA, SB>(n)]; };
   auto pre = [&](int slot, int, int k) MRDFT_INL {
     ea[slot] = __ldcs(yprev + k);
     eb[slot] = __ldcs(yprev + h + k);
@@ -291,10 +292,11 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_fwd_window(const FwdArgs a) 
 }
 
 static constexpr size_t kColsSmem =
-    (size_t)(pad8_size(1 << kPassElemsLog) + twq_size(12) + (1 << (kPassElemsLog - 3))) * sizeof(float2);
-// twiddle tables of the rows pass: KC (64 + 1) + KC (C / 64 + 1) <= 4 * 65 + 2^(E-6) + 4
-constexpr size_t rows_smem(int E) {
-  return (size_t)(pad8_size(1 << E) + twq_size(E) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
+    (size_t)((1 << kPassElemsLog) + twq_size(12) + (1 << (kPassElemsLog - 3))) * sizeof(float2);
+// rows pass: work area, w_C table, twiddle tables KC (64 + 1) + KC (C / 64 + 1)
+// <= 4 * 65 + 2^(E-6) + 4
+constexpr size_t rows_smem(int E, int CB) {
+  return (size_t)((1 << E) + twq_size(CB) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
 }
 
 // =============================================================== two-pass
@@ -313,8 +315,8 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(const FwdArgs a) {
   constexpr int PTS = (1 << E) / NT;
   constexpr int RCB = E - QB, RC = 1 << RCB;
   extern __shared__ __align__(1024) float2 sm[];
-  float2* S = sm;                            // column r position q: q RC + r (XOR, then pad8)
-  float2* TQ = sm + pad8_size(1 << E);       // quarter-wave w_{2^12}
+  float2* S = sm;                            // column r position q: q RC + r (staging, then zlay)
+  float2* TQ = sm + (1 << E);                // quarter-wave w_{2^12}
   float2* ZC = TQ + twq_size(12);            // w_{2^i}^(r0 + r), r < RC
   if ((int)blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
@@ -348,44 +350,56 @@ __global__ void __launch_bounds__(NT, 2) k_fwd_cols(const FwdArgs a) {
     for (int t = 0; t < 8; ++t) {
       const int e = threadIdx.x + (t0 + t) * NT;
       const float2 w = cmul(ZC[e & (RC - 1)], twq_l(tw, QB + 1, e >> RCB));
-      S[swzf(e)] = cmul(csub(xa[t], xb[t]), w);  // e = q RC + r
+      S[stg<6, 0>(e)] = cmul(csub(xa[t], xb[t]), w);  // e = q RC + r
     }
   }
   __syncthreads();
   float2* F = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[swzf((n << RCB) + b)]; };
+  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[stg<6, 0>((n << RCB) + b)]; };
   auto sink = [&](int, int b, int k2, float2 v) MRDFT_INL { __stcg(F + ((int64_t)k2 << CB) + r0 + b, v); };
-  cg_fft<QB, QB, NT, PTS, true, kPreNone>(S, QB, RCB, tw, src, NoPre{}, sink);
+  cg_fft<QB, QB, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
 template <int E, int NT, int CB>
-__global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_fwd_rows(const FwdArgs a) {
+__global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_fwd_rows(const FwdArgs a) {
   constexpr int PTS = (1 << E) / NT;
   constexpr int C = 1 << CB;
   constexpr int KCB = E - CB, KC = 1 << KCB;
   constexpr int HU = C >> 6;               // rows of the high twiddle table
+  constexpr int SH = E - kPassElemsLog;    // CTAs per item: 2^-SH (SH < 0), items per CTA: 2^SH
+  constexpr int SA = CB <= 12 ? 4 : 3, SB = CB <= 12 ? 6 : 9;  // staging layout
   extern __shared__ __align__(1024) float2 sm[];
-  float2* S = sm;                          // sequence j position r at r KC + j (XOR, then pad8)
-  float2* TQ = sm + pad8_size(1 << E);     // quarter-wave w_{2^E}
-  float2* TWL = TQ + twq_size(E);          // [KC][64] (row stride 65): w_h^(k2 t)
+  float2* S = sm;                          // sequence j position r at r KC + j (staging, then zlay)
+  float2* TQ = sm + (1 << E);              // quarter-wave w_C
+  float2* TWL = TQ + twq_size(CB);         // [KC][64] (row stride 65): w_h^(k2 t)
   float2* TWH = TWL + 4 * 65;              // [KC][C/64] (row stride C/64 + 1): w_h^(k2 64 u)
-  const int item = (int)blockIdx.x << (E - kPassElemsLog);
+  int item, blk;
+  if constexpr (SH >= 0) {
+    item = (int)blockIdx.x << SH;
+  } else {
+    item = (int)blockIdx.x >> -SH;
+  }
   if (item >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
+  if constexpr (SH >= 0) {
+    blk = it.block >> SH;
+  } else {
+    blk = (it.block << -SH) | ((int)blockIdx.x & ((1 << -SH) - 1));
+  }
   const int i = a.level;
   const int HB = i - 1, QB = HB - CB;
   const int64_t h = (int64_t)1 << HB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t ws = (int64_t)it.window << i;
-  const int k0 = (it.block >> (E - kPassElemsLog)) << KCB;
+  const int k0 = blk << KCB;
   const float2* F = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
   const float2* __restrict__ yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
 #pragma unroll 8
   for (int e = threadIdx.x; e < KC * C; e += NT) {
     const int r = e & (C - 1), j = e >> CB;
-    cp_async8(S + swzf((r << KCB) + j), F + ((int64_t)(k0 + j) << CB) + r);
+    cp_async8(S + stg<SA, SB>((r << KCB) + j), F + ((int64_t)(k0 + j) << CB) + r);
   }
-  load_twq<NT>(TQ, E, a.tw);
+  load_twq<NT>(TQ, CB, a.tw);
   for (int t = threadIdx.x; t < KC * (64 + HU); t += NT) {
     if (t < KC * 64) {
       const int j = t >> 6, u = t & 63;
@@ -399,29 +413,33 @@ __global__ void __launch_bounds__(NT, E == kPassElemsLog ? 2 : 1) k_fwd_rows(con
   __syncthreads();
   // the intermediate rows are dead now: drop them from L2 without write-back
   for (int l = threadIdx.x; l < KC * C / 16; l += NT) discard_l2(F + ((int64_t)k0 << CB) + 16 * l);
-  const TwQ tw{TQ, E};
+  const TwQ tw{TQ, CB};
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
   // w_h^(r k2) = w_h^(k2 (r mod 64)) w_h^(k2 64 (r / 64))
   auto src = [&](int b, int n) MRDFT_INL -> float2 {
-    return cmul(S[swzf((n << KCB) + b)], cmul(TWL[b * 65 + (n & 63)], TWH[b * (HU + 1) + (n >> 6)]));
+    return cmul(S[stg<SA, SB>((n << KCB) + b)], cmul(TWL[b * 65 + (n & 63)], TWH[b * (HU + 1) + (n >> 6)]));
   };
   const bool reread = sd.m > i;
-  float2 ea[PTS], eb[PTS];
-  // U (Eq. 2): the children of bin k, read once per group of 8 bins
-  auto pre = [&](int slot, int b, int k1) MRDFT_INL {
+  auto store = [&](int b, int k1, float2 ev, float2 odd) MRDFT_INL {
     const int64_t k = ((int64_t)k1 << QB) + k0 + b;
-    ea[slot] = __ldcs(yprev + k);
-    eb[slot] = __ldcs(yprev + h + k);
-  };
-  auto sink = [&](int slot, int b, int k1, float2 odd) MRDFT_INL {
-    const int64_t k = ((int64_t)k1 << QB) + k0 + b;
-    const float2 ev = cadd(ea[slot], eb[slot]);
     const float4 v = make_float4(ev.x, ev.y, odd.x, odd.y);
     float4* dst = reinterpret_cast<float4*>(ycur + 2 * k);
     if (reread) __stcg(dst, v);
     else __stcs(dst, v);
   };
-  cg_fft<CB, CB, NT, PTS, true, kPreGroup>(S, CB, KCB, tw, src, pre, sink);
+  {
+    float2 ea[PTS], eb[PTS];
+    // U (Eq. 2): the children of bin k, read once per group of 8 bins
+    auto pre = [&](int slot, int b, int k1) MRDFT_INL {
+      const int64_t k = ((int64_t)k1 << QB) + k0 + b;
+      ea[slot] = __ldcs(yprev + k);
+      eb[slot] = __ldcs(yprev + h + k);
+    };
+    auto sink = [&](int slot, int b, int k1, float2 odd) MRDFT_INL {
+      store(b, k1, cadd(ea[slot], eb[slot]), odd);
+    };
+    cg_fft<CB, CB, NT, PTS, true, kPreGroup, KCB>(S, CB, KCB, tw, src, pre, sink);
+  }
 }
 
 // Launch-time dispatch to the instantiation of a level's FFT sizes.
@@ -430,10 +448,12 @@ void cols_launch(const FwdArgs& a, int grid, cudaStream_t s) {
   k_fwd_cols<kPassThreads, QB><<<grid, kPassThreads, kColsSmem, s>>>(a);
 }
 template <int CB>
+constexpr int rows_e() { return rows_elems_log_c(CB); }
+template <int CB>
 void rows_launch(const FwdArgs& a, int grid, cudaStream_t s) {
-  constexpr int E = CB > kPassElemsLog ? CB : kPassElemsLog;
-  constexpr int NT = E == kPassElemsLog ? kPassThreads : kPassThreadsWide;
-  k_fwd_rows<E, NT, CB><<<grid >> (E - kPassElemsLog), NT, rows_smem(E), s>>>(a);
+  constexpr int E = rows_e<CB>();
+  constexpr int NT = E <= kPassElemsLog ? kPassThreads : kPassThreadsWide;
+  k_fwd_rows<E, NT, CB><<<rows_grid(a.level, false, grid), NT, rows_smem(E, CB), s>>>(a);
 }
 template <int QB>
 cudaError_t cols_attr() {
@@ -442,16 +462,17 @@ cudaError_t cols_attr() {
 }
 template <int CB>
 cudaError_t rows_attr() {
-  constexpr int E = CB > kPassElemsLog ? CB : kPassElemsLog;
-  constexpr int NT = E == kPassElemsLog ? kPassThreads : kPassThreadsWide;
-  return cudaFuncSetAttribute(k_fwd_rows<E, NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rows_smem(E));
+  constexpr int E = rows_e<CB>();
+  constexpr int NT = E <= kPassElemsLog ? kPassThreads : kPassThreadsWide;
+  return cudaFuncSetAttribute(k_fwd_rows<E, NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)rows_smem(E, CB));
 }
 
 // ================================================================ launchers
 
 static constexpr size_t kTileSmem =
-    (size_t)(kTile + pad16_size(kTile) + pad8_size(kTile / 2) + twq_size(kTileLog)) * sizeof(float2) + kMaxPack * sizeof(TileSig);
-static constexpr size_t kWinSmem = (size_t)(pad8_size(1 << kWinMaxLog) + twq_size(13)) * sizeof(float2);
+    (size_t)(kTile + pad16_size(kTile) + kTile / 2 + twq_size(kTileLog)) * sizeof(float2) + kMaxPack * sizeof(TileSig);
+static constexpr size_t kWinSmem = (size_t)((1 << kWinMaxLog) + twq_size(13)) * sizeof(float2);
 static_assert((1 << kWinMaxLog) % kWinThreads == 0, "points per thread");
 cudaError_t set_fwd_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_fwd_tile<kTileLog, kTileThreads>,
@@ -485,14 +506,14 @@ cudaError_t launch_fwd_window(const FwdArgs& a, int grid, cudaStream_t s) {
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s) {
-  const int QB = (a.level - 1) - cols_log(a.level);
+  const int QB = (a.level - 1) - cols_log(a.level, false);
   static_for_host<3, 12>([&](auto Q) {
     if (QB == decltype(Q)::value) cols_launch<decltype(Q)::value>(a, grid, s);
   });
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_rows(const FwdArgs& a, int grid, cudaStream_t s) {
-  const int CB = cols_log(a.level);
+  const int CB = cols_log(a.level, false);
   static_for_host<11, 15>([&](auto C) {
     if (CB == decltype(C)::value) rows_launch<decltype(C)::value>(a, grid, s);
   });

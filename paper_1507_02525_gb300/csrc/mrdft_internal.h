@@ -43,17 +43,27 @@ constexpr int kTileThreads = 256;            // 16 samples per thread, 2 CTAs pe
 constexpr int kWinMaxLog = 13;               // one CTA FFT holds up to 2^13 points
 constexpr int kWinThreads = 256;             // levels 13, 14: 16 or 32 points per thread
 // Two-pass levels (i >= 15), h = 2^(i-1) = Q * C with C = 2^cols_log(i):
-// 2^11 up to level 23, then 2^(i-12) so that Q <= 2^11.
+//   forward: 2^11 up to level 23, then 2^(i-12); adjoint: 2^10 up to level
+//   22, then 2^(i-12) -- so that Q <= 2^11 and every cols CTA reads chunks of
+//   at least 4 consecutive samples.
 //   cols pass: 2^13 points per CTA (RC = 2^13 / Q chunk offsets), 2 CTAs/SM
-//   rows pass: 2^rows_elems_log(i) points per CTA (KC = 2^E / C residues)
+//   rows pass: 2^rows_elems_log(i) points per CTA (KC = 2^E / C residues):
+//   2^13 (2^14 for C = 2^14); the adjoint's C = 2^10 rows use 2^12.
 constexpr int kPassElemsLog = 13;
-constexpr int kPassThreads = 256;        // 2^13-point CTAs: 32 points per thread
+constexpr int kPassThreads = 256;        // 2^12- and 2^13-point CTAs
 constexpr int kPassThreadsWide = 512;    // the 2^14-point rows CTA (level 26)
-__host__ __device__ constexpr int cols_log(int i) { return (i - 1) - 11 > 11 ? (i - 1) - 11 : 11; }
-__host__ __device__ constexpr int rows_elems_log(int i) { return cols_log(i) > 13 ? cols_log(i) : 13; }
+__host__ __device__ constexpr int cols_log(int i, bool adj) {
+  return (i - 1) - 11 > (adj ? 10 : 11) ? (i - 1) - 11 : (adj ? 10 : 11);
+}
+__host__ __device__ constexpr int rows_elems_log_c(int cb) { return cb <= 10 ? 12 : (cb > 13 ? cb : 13); }
+__host__ __device__ constexpr int rows_elems_log(int i, bool adj) { return rows_elems_log_c(cols_log(i, adj)); }
 // work items of a two-pass level, per window: one per cols CTA (2^(i-14));
-// a rows CTA of 2^E points takes every 2^(E-13)-th item
+// a rows CTA of 2^E points takes 2^(E-13) items (E >= 13) or half an item
 __host__ __device__ constexpr int pass_items(int i) { return 1 << ((i - 1) - kPassElemsLog); }
+__host__ __device__ constexpr int rows_grid(int i, bool adj, int items) {
+  return rows_elems_log(i, adj) >= kPassElemsLog ? items >> (rows_elems_log(i, adj) - kPassElemsLog)
+                                                 : items << (kPassElemsLog - rows_elems_log(i, adj));
+}
 
 struct FwdArgs {
   const void* x;  // float2* (complex64) or float* (real FP32)
