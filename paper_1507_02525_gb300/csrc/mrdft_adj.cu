@@ -456,7 +456,7 @@ void adj_cols_launch(const AdjArgs& a, int grid, cudaStream_t s) {
 template <int CB>
 void adj_rows_launch(const AdjArgs& a, int grid, cudaStream_t s) {
   constexpr int E = adj_rows_e<CB>();
-  constexpr int NT = E <= kPassElemsLog ? kPassThreads : kPassThreadsWide;
+  constexpr int NT = E < kPassElemsLog ? kColsThreads : (E == kPassElemsLog ? kPassThreads : kPassThreadsWide);
   k_adj_rows<E, NT, CB><<<rows_grid(a.level, true, grid), NT, adj_rows_smem(E, CB), s>>>(a);
 }
 template <int QB>
@@ -467,7 +467,7 @@ cudaError_t adj_cols_attr() {
 template <int CB>
 cudaError_t adj_rows_attr() {
   constexpr int E = adj_rows_e<CB>();
-  constexpr int NT = E <= kPassElemsLog ? kPassThreads : kPassThreadsWide;
+  constexpr int NT = E < kPassElemsLog ? kColsThreads : (E == kPassElemsLog ? kPassThreads : kPassThreadsWide);
   return cudaFuncSetAttribute(k_adj_rows<E, NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)adj_rows_smem(E, CB));
 }

@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_fwd_rows(con
 // Launch-time dispatch to the instantiation of a level's FFT sizes.
 template <int QB>
 void cols_launch(const FwdArgs& a, int grid, cudaStream_t s) {
-  k_fwd_cols<kPassThreads, QB><<<grid, kPassThreads, kColsSmem, s>>>(a);
+  k_fwd_cols<kColsThreads, QB><<<grid, kColsThreads, kColsSmem, s>>>(a);
 }
 template <int CB>
 constexpr int rows_e() { return rows_elems_log_c(CB); }
@@ -457,7 +457,7 @@ void rows_launch(const FwdArgs& a, int grid, cudaStream_t s) {
 }
 template <int QB>
 cudaError_t cols_attr() {
-  return cudaFuncSetAttribute(k_fwd_cols<kPassThreads, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_fwd_cols<kColsThreads, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kColsSmem);
 }
 template <int CB>

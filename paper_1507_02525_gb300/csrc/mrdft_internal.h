@@ -50,7 +50,8 @@ constexpr int kWinThreads = 256;             // levels 13, 14: 16 or 32 points p
 //   rows pass: 2^rows_elems_log(i) points per CTA (KC = 2^E / C residues):
 //   2^13 (2^14 for C = 2^14); the adjoint's C = 2^10 rows use 2^12.
 constexpr int kPassElemsLog = 13;
-constexpr int kPassThreads = 256;        // 2^12- and 2^13-point CTAs
+constexpr int kPassThreads = 256;        // 2^13-point rows / adjoint cols CTAs
+constexpr int kColsThreads = 512;        // forward cols and 2^12-point adjoint rows CTAs (64 registers)
 constexpr int kPassThreadsWide = 512;    // the 2^14-point rows CTA (level 26)
 __host__ __device__ constexpr int cols_log(int i, bool adj) {
   return (i - 1) - 11 > (adj ? 10 : 11) ? (i - 1) - 11 : (adj ? 10 : 11);
