@@ -445,13 +445,13 @@ __global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
       __stcg(acc + h + n, make_float2(-c.x, -c.y));
     }
   };
-  cg_fft<QB, QB, NT, PTS, true, kPreGroup, (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, pre, sink);
+  cg_fft<QB, QB, NT, PTS, true, (NT > 256 ? kPreHalf : kPreGroup), (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, pre, sink);
 }
 
 // Launch-time dispatch to the instantiation of a level's FFT sizes.
 template <int QB>
 void adj_cols_launch(const AdjArgs& a, int grid, cudaStream_t s) {
-  k_adj_cols<kPassThreads, QB><<<grid, kPassThreads, kAdjColsSmem, s>>>(a);
+  k_adj_cols<kColsThreads, QB><<<grid, kColsThreads, kAdjColsSmem, s>>>(a);
 }
 template <int CB>
 void adj_rows_launch(const AdjArgs& a, int grid, cudaStream_t s) {
@@ -461,7 +461,7 @@ void adj_rows_launch(const AdjArgs& a, int grid, cudaStream_t s) {
 }
 template <int QB>
 cudaError_t adj_cols_attr() {
-  return cudaFuncSetAttribute(k_adj_cols<kPassThreads, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  return cudaFuncSetAttribute(k_adj_cols<kColsThreads, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)kAdjColsSmem);
 }
 template <int CB>

@@ -109,10 +109,11 @@ __device__ __forceinline__ int drev8(int v, int d) {
 //   kPreBarrier: before the barrier that separates every read of this pass
 //   from the sink's writes (the caller may read what the sink overwrites);
 //   kPreGroup: after each group's DFT, for the group's R bins, before their
-//   sinks (global reads issued in one batch per group, few registers held).
+//   sinks (global reads issued in one batch per group, few registers held);
+//   kPreHalf: the same in batches of R/2 bins (fewer registers still).
 // Every thread loads all its groups before the pass's barrier, so the pass is
 // in place; PTS bounds the points per thread (NT * PTS >= points per pass).
-constexpr int kPreNone = 0, kPreBarrier = 1, kPreGroup = 2;
+constexpr int kPreNone = 0, kPreBarrier = 1, kPreGroup = 2, kPreHalf = 3;
 
 template <int RB, int NT, int PTS, bool SEQ_MINOR, bool FIRST, bool LAST, int PRE, int ZS, class Src, class Pre, class Sink>
 __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq_log, int SH, int P, const TwQ& tw,
@@ -173,12 +174,22 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
     }
     dft_reg<R>(v[j]);
     if constexpr (LAST) {
-      if constexpr (PRE == kPreGroup) {
+      if constexpr (PRE == kPreHalf && R >= 2) {
 #pragma unroll
-        for (int k = 0; k < R; ++k) pre(j * R + k, b, g + (k << LRB));
+        for (int k0 = 0; k0 < R; k0 += R / 2) {
+#pragma unroll
+          for (int k = k0; k < k0 + R / 2; ++k) pre(j * R + k, b, g + (k << LRB));
+#pragma unroll
+          for (int k = k0; k < k0 + R / 2; ++k) sink(j * R + k, b, g + (k << LRB), v[j][k]);
+        }
+      } else {
+        if constexpr (PRE == kPreGroup || PRE == kPreHalf) {
+#pragma unroll
+          for (int k = 0; k < R; ++k) pre(j * R + k, b, g + (k << LRB));
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) sink(j * R + k, b, g + (k << LRB), v[j][k]);
       }
-#pragma unroll
-      for (int k = 0; k < R; ++k) sink(j * R + k, b, g + (k << LRB), v[j][k]);
     } else {
       const int a0 = SEQ_MINOR ? ((g << nseq_log) + b) : ((b << LB) + g);
 #pragma unroll

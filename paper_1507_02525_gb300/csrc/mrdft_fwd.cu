@@ -438,7 +438,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_fwd_rows(con
     auto sink = [&](int slot, int b, int k1, float2 odd) MRDFT_INL {
       store(b, k1, cadd(ea[slot], eb[slot]), odd);
     };
-    cg_fft<CB, CB, NT, PTS, true, kPreGroup, KCB>(S, CB, KCB, tw, src, pre, sink);
+    cg_fft<CB, CB, NT, PTS, true, (NT > 256 ? kPreHalf : kPreGroup), KCB>(S, CB, KCB, tw, src, pre, sink);
   }
 }
 
@@ -452,7 +452,7 @@ constexpr int rows_e() { return rows_elems_log_c(CB); }
 template <int CB>
 void rows_launch(const FwdArgs& a, int grid, cudaStream_t s) {
   constexpr int E = rows_e<CB>();
-  constexpr int NT = E <= kPassElemsLog ? kPassThreads : kPassThreadsWide;
+  constexpr int NT = E <= kPassElemsLog ? kColsThreads : kPassThreadsWide;
   k_fwd_rows<E, NT, CB><<<rows_grid(a.level, false, grid), NT, rows_smem(E, CB), s>>>(a);
 }
 template <int QB>
@@ -463,7 +463,7 @@ cudaError_t cols_attr() {
 template <int CB>
 cudaError_t rows_attr() {
   constexpr int E = rows_e<CB>();
-  constexpr int NT = E <= kPassElemsLog ? kPassThreads : kPassThreadsWide;
+  constexpr int NT = E <= kPassElemsLog ? kColsThreads : kPassThreadsWide;
   return cudaFuncSetAttribute(k_fwd_rows<E, NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)rows_smem(E, CB));
 }
