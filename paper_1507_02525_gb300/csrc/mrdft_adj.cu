@@ -145,13 +145,25 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     }
     const float2* Ein = E[(i + 1) & 1];
     float2* Eout = E[i & 1];
-    // G_i = g_i + P_i: even half -> Eout, conj(odd half) -> Z
-#pragma unroll 4
-    for (int c = tid; c < (Tn >> 1); c += NT) {
+    // G_i = g_i + P_i: even half -> Eout, conj(odd half) -> Z; every gradient
+    // pair of the thread is requested before the first is used
+    constexpr int ITER = T / 2 / NT;
+    float4 gv[ITER];
+#pragma unroll
+    for (int q = 0; q < ITER; ++q) {
+      const int c = tid + q * NT;
+      if (c < (Tn >> 1)) {
+        const int e = c << 1;
+        const AdjTileSig& ts = TS[e >> tl];
+        gv[q] = __ldcs(reinterpret_cast<const float4*>(a.gy + ts.g_base + ((int64_t)(i - 1) << ts.m) + (e & ((1 << tl) - 1))));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < ITER; ++q) {
+      const int c = tid + q * NT;
+      if (c >= (Tn >> 1)) continue;
       const int e = c << 1;
-      const AdjTileSig& ts = TS[e >> tl];
-      const int off = e & ((1 << tl) - 1);
-      float4 g = __ldcs(reinterpret_cast<const float4*>(a.gy + ts.g_base + ((int64_t)(i - 1) << ts.m) + off));
+      const float4 g = gv[q];
       const int w = e >> i, k = e & (L - 1);
       float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
       if (i == tl) {
