@@ -309,8 +309,11 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) 
   cg_fft<LB, LB, NT, PTS, false, kPreGroup>(Z, LB, 0, tw, src, pre, sink);
 }
 
-static constexpr size_t kAdjColsSmem =
-    (size_t)((1 << kPassElemsLog) + twq_size(12) + (1 << (kPassElemsLog - 3))) * sizeof(float2);
+constexpr size_t adj_cols_smem(int E) {
+  return (size_t)((1 << E) + twq_size(12) + (1 << (E - 3))) * sizeof(float2);
+}
+template <int QB>
+constexpr int adj_cols_e() { return kPassElemsLog; }
 constexpr size_t adj_rows_smem(int E, int CB) {
   return (size_t)((1 << E) + twq_size(CB) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
 }
@@ -397,23 +400,24 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
 // cols: item (sig, window, c) covers chunk offsets r in [r0, r0 + RC),
 //   r0 = c RC, RC = 2^13 / Q: U[window][k2][r] -> IDFT_Q over k2 -> zb[r + C q]
 //   -> conj(w_{2^i}^n) zb added to acc at n and subtracted at h + n.
-template <int NT, int QB>
-__global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
-  constexpr int E = kPassElemsLog;
+template <int NT, int QB, int E>
+__global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_adj_cols(const AdjArgs a) {
   constexpr int PTS = (1 << E) / NT;
+  constexpr int SH = kPassElemsLog - E;      // CTAs per item: 2^SH
   constexpr int RCB = E - QB, RC = 1 << RCB;
   extern __shared__ __align__(1024) float2 sm[];
   float2* S = sm;                          // column r position k2 at k2 RC + r (staging, then zlay)
   float2* TQ = sm + (1 << E);              // quarter-wave w_{2^12}
   float2* ZC = TQ + twq_size(12);          // w_{2^i}^(r0 + r), r < RC
-  if ((int)blockIdx.x >= a.nitems) return;
-  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  const int item = (int)blockIdx.x >> SH;
+  if (item >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
   const int i = a.level;
   const int HB = i - 1, CB = HB - QB;
   const int64_t h = (int64_t)1 << HB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
-  const int r0 = it.block << RCB;
+  const int r0 = ((it.block << SH) | ((int)blockIdx.x & ((1 << SH) - 1))) << RCB;
   const float2* U = a.scratch + sd.aux_off + (w << HB);
   float2* acc = a.acc + sd.in_off + (w << i);
   const bool add = sd.m > i;
@@ -457,13 +461,15 @@ __global__ void __launch_bounds__(NT, 2) k_adj_cols(const AdjArgs a) {
       __stcg(acc + h + n, make_float2(-c.x, -c.y));
     }
   };
-  cg_fft<QB, QB, NT, PTS, true, (NT > 256 ? kPreHalf : kPreGroup), (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, pre, sink);
+  cg_fft<QB, QB, NT, PTS, true, kPreHalf, (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, pre, sink);
 }
 
 // Launch-time dispatch to the instantiation of a level's FFT sizes.
 template <int QB>
 void adj_cols_launch(const AdjArgs& a, int grid, cudaStream_t s) {
-  k_adj_cols<kColsThreads, QB><<<grid, kColsThreads, kAdjColsSmem, s>>>(a);
+  constexpr int E = adj_cols_e<QB>();
+  constexpr int NT = E < kPassElemsLog ? kPassThreads : kColsThreads;
+  k_adj_cols<NT, QB, E><<<grid << (kPassElemsLog - E), NT, adj_cols_smem(E), s>>>(a);
 }
 template <int CB>
 void adj_rows_launch(const AdjArgs& a, int grid, cudaStream_t s) {
@@ -473,8 +479,10 @@ void adj_rows_launch(const AdjArgs& a, int grid, cudaStream_t s) {
 }
 template <int QB>
 cudaError_t adj_cols_attr() {
-  return cudaFuncSetAttribute(k_adj_cols<kColsThreads, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kAdjColsSmem);
+  constexpr int E = adj_cols_e<QB>();
+  constexpr int NT = E < kPassElemsLog ? kPassThreads : kColsThreads;
+  return cudaFuncSetAttribute(k_adj_cols<NT, QB, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)adj_cols_smem(E));
 }
 template <int CB>
 cudaError_t adj_rows_attr() {

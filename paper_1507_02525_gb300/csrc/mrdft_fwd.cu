@@ -291,8 +291,11 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_fwd_window(const FwdArgs a) 
   cg_fft<LB, LB, NT, PTS, false, kPreGroup>(Z, LB, 0, tw, src, pre, sink);
 }
 
-static constexpr size_t kColsSmem =
-    (size_t)((1 << kPassElemsLog) + twq_size(12) + (1 << (kPassElemsLog - 3))) * sizeof(float2);
+// cols pass: work area 2^E, w_{2^12} table, chunk twiddles (RC <= 2^(E-3))
+constexpr size_t cols_smem(int E) { return (size_t)((1 << E) + twq_size(12) + (1 << (E - 3))) * sizeof(float2); }
+// cols CTAs of 2^12 points (4 per SM) where Q <= 2^10 keeps chunks of >= 4
+template <int QB>
+constexpr int cols_e() { return QB <= 10 ? 12 : kPassElemsLog; }
 // rows pass: work area, w_C table, twiddle tables KC (64 + 1) + KC (C / 64 + 1)
 // <= 4 * 65 + 2^(E-6) + 4
 constexpr size_t rows_smem(int E, int CB) {
@@ -309,22 +312,23 @@ constexpr size_t rows_smem(int E, int CB) {
 // rows: a CTA of 2^E points covers residues k2 in [k0, k0 + KC), KC = 2^E / C:
 //   F[window][k2][.] times w_h^(r k2) -> DFT_C -> odd bin Q k1 + k2; even bin
 //   from the children; (even, odd) pairs stored at 2k.
-template <int NT, int QB>
-__global__ void __launch_bounds__(NT, 2) k_fwd_cols(const FwdArgs a) {
-  constexpr int E = kPassElemsLog;
+template <int NT, int QB, int E>
+__global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_fwd_cols(const FwdArgs a) {
   constexpr int PTS = (1 << E) / NT;
+  constexpr int SH = kPassElemsLog - E;      // CTAs per item: 2^SH
   constexpr int RCB = E - QB, RC = 1 << RCB;
   extern __shared__ __align__(1024) float2 sm[];
   float2* S = sm;                            // column r position q: q RC + r (staging, then zlay)
   float2* TQ = sm + (1 << E);                // quarter-wave w_{2^12}
   float2* ZC = TQ + twq_size(12);            // w_{2^i}^(r0 + r), r < RC
-  if ((int)blockIdx.x >= a.nitems) return;
-  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  const int item = (int)blockIdx.x >> SH;
+  if (item >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
   const int i = a.level;
   const int HB = i - 1, CB = HB - QB;
   const SigDesc sd = a.sigs[it.sig];
   const int64_t xs = sd.in_off + ((int64_t)it.window << i);
-  const int r0 = it.block << RCB;
+  const int r0 = ((it.block << SH) | ((int)blockIdx.x & ((1 << SH) - 1))) << RCB;
   const int64_t h = (int64_t)1 << HB;
   // x rows r0 .. r0 + RC of every chunk q, both halves: start moving them into
   // L2 (the loads below come in batches)
@@ -445,7 +449,9 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_fwd_rows(con
 // Launch-time dispatch to the instantiation of a level's FFT sizes.
 template <int QB>
 void cols_launch(const FwdArgs& a, int grid, cudaStream_t s) {
-  k_fwd_cols<kColsThreads, QB><<<grid, kColsThreads, kColsSmem, s>>>(a);
+  constexpr int E = cols_e<QB>();
+  constexpr int NT = E < kPassElemsLog ? kPassThreads : kColsThreads;
+  k_fwd_cols<NT, QB, E><<<grid << (kPassElemsLog - E), NT, cols_smem(E), s>>>(a);
 }
 template <int CB>
 constexpr int rows_e() { return rows_elems_log_c(CB); }
@@ -457,8 +463,9 @@ void rows_launch(const FwdArgs& a, int grid, cudaStream_t s) {
 }
 template <int QB>
 cudaError_t cols_attr() {
-  return cudaFuncSetAttribute(k_fwd_cols<kColsThreads, QB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)kColsSmem);
+  constexpr int E = cols_e<QB>();
+  constexpr int NT = E < kPassElemsLog ? kPassThreads : kColsThreads;
+  return cudaFuncSetAttribute(k_fwd_cols<NT, QB, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cols_smem(E));
 }
 template <int CB>
 cudaError_t rows_attr() {
