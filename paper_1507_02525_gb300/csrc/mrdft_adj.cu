@@ -315,10 +315,10 @@ constexpr size_t adj_cols_smem(int E) {
 template <int QB>
 constexpr int adj_cols_e() { return kPassElemsLog; }
 constexpr size_t adj_rows_smem(int E, int CB) {
-  return (size_t)((1 << E) + twq_size(CB) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
+  return (size_t)((1 << E) + twq_size(CB) + 4 * 65 + (1 << (E - 6)) + 16) * sizeof(float2);
 }
 template <int CB>
-constexpr int adj_rows_e() { return rows_elems_log_c(CB); }
+constexpr int adj_rows_e() { return rows_elems_log_c(CB, true); }
 
 // =============================================================== two-pass
 
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
   float2* S = sm;                          // sequence j at j C (staging, then zlay)
   float2* TQ = sm + (1 << E);              // quarter-wave w_C
   float2* TWL = TQ + twq_size(CB);         // [KC][64] (row stride 65): w_h^(k2 t)
-  float2* TWH = TWL + 4 * 65;              // [KC][C/64] (row stride C/64 + 1): w_h^(k2 64 u)
+  float2* TWH = TWL + 4 * 65;              // [KC][C/64] (row stride C/64 + 16/KC): w_h^(k2 64 u)
   int item, blk;
   if constexpr (SH >= 0) {
     item = (int)blockIdx.x << SH;
@@ -383,7 +383,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
       TWL[j * 65 + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * u);
     } else {
       const int t2 = t - KC * 64, j = t2 / HU, u = t2 % HU;
-      TWH[j * (HU + 1) + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * 64 * u);
+      TWH[j * (HU + 16 / KC) + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * 64 * u);
     }
   }
   __syncthreads();
@@ -391,7 +391,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
   float2* U = a.scratch + sd.aux_off + (w << HB);
   auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[stg<SA, SB>((b << CB) + n)]; };
   auto sink = [&](int, int b, int r, float2 v) MRDFT_INL {
-    const float2 t = cmul(TWL[b * 65 + (r & 63)], TWH[b * (HU + 1) + (r >> 6)]);
+    const float2 t = cmul(TWL[b * 65 + (r & 63)], TWH[b * (HU + 16 / KC) + (r >> 6)]);
     __stcg(U + ((int64_t)(k0 + b) << CB) + r, cmulc(conjf2(v), t));
   };
   cg_fft<CB, CB, NT, PTS, false, kPreNone>(S, CB, KCB, tw, src, NoPre{}, sink);

@@ -299,7 +299,7 @@ constexpr int cols_e() { return QB <= 10 ? 12 : kPassElemsLog; }
 // rows pass: work area, w_C table, twiddle tables KC (64 + 1) + KC (C / 64 + 1)
 // <= 4 * 65 + 2^(E-6) + 4
 constexpr size_t rows_smem(int E, int CB) {
-  return (size_t)((1 << E) + twq_size(CB) + 4 * 65 + (1 << (E - 6)) + 4) * sizeof(float2);
+  return (size_t)((1 << E) + twq_size(CB) + 4 * 65 + (1 << (E - 6)) + 16) * sizeof(float2);
 }
 
 // =============================================================== two-pass
@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_fwd_cols(cons
 }
 
 template <int E, int NT, int CB>
-__global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_fwd_rows(const FwdArgs a) {
+__global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : (E == kPassElemsLog ? 2 : 1)) k_fwd_rows(const FwdArgs a) {
   constexpr int PTS = (1 << E) / NT;
   constexpr int C = 1 << CB;
   constexpr int KCB = E - CB, KC = 1 << KCB;
@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_fwd_rows(con
   float2* S = sm;                          // sequence j position r at r KC + j (staging, then zlay)
   float2* TQ = sm + (1 << E);              // quarter-wave w_C
   float2* TWL = TQ + twq_size(CB);         // [KC][64] (row stride 65): w_h^(k2 t)
-  float2* TWH = TWL + 4 * 65;              // [KC][C/64] (row stride C/64 + 1): w_h^(k2 64 u)
+  float2* TWH = TWL + 4 * 65;              // [KC][C/64] (row stride C/64 + 16/KC): w_h^(k2 64 u)
   int item, blk;
   if constexpr (SH >= 0) {
     item = (int)blockIdx.x << SH;
@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_fwd_rows(con
       TWL[j * 65 + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * u);
     } else {
       const int t2 = t - KC * 64, j = t2 / HU, u = t2 % HU;
-      TWH[j * (HU + 1) + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * 64 * u);
+      TWH[j * (HU + 16 / KC) + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * 64 * u);
     }
   }
   cp_async_wait_all();
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_fwd_rows(con
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
   // w_h^(r k2) = w_h^(k2 (r mod 64)) w_h^(k2 64 (r / 64))
   auto src = [&](int b, int n) MRDFT_INL -> float2 {
-    return cmul(S[stg<SA, SB>((n << KCB) + b)], cmul(TWL[b * 65 + (n & 63)], TWH[b * (HU + 1) + (n >> 6)]));
+    return cmul(S[stg<SA, SB>((n << KCB) + b)], cmul(TWL[b * 65 + (n & 63)], TWH[b * (HU + 16 / KC) + (n >> 6)]));
   };
   const bool reread = sd.m > i;
   auto store = [&](int b, int k1, float2 ev, float2 odd) MRDFT_INL {
@@ -442,7 +442,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_fwd_rows(con
     auto sink = [&](int slot, int b, int k1, float2 odd) MRDFT_INL {
       store(b, k1, cadd(ea[slot], eb[slot]), odd);
     };
-    cg_fft<CB, CB, NT, PTS, true, (NT > 256 ? kPreHalf : kPreGroup), KCB>(S, CB, KCB, tw, src, pre, sink);
+    cg_fft<CB, CB, NT, PTS, true, kPreHalf, KCB>(S, CB, KCB, tw, src, pre, sink);
   }
 }
 
@@ -454,11 +454,11 @@ void cols_launch(const FwdArgs& a, int grid, cudaStream_t s) {
   k_fwd_cols<NT, QB, E><<<grid << (kPassElemsLog - E), NT, cols_smem(E), s>>>(a);
 }
 template <int CB>
-constexpr int rows_e() { return rows_elems_log_c(CB); }
+constexpr int rows_e() { return rows_elems_log_c(CB, false); }
 template <int CB>
 void rows_launch(const FwdArgs& a, int grid, cudaStream_t s) {
   constexpr int E = rows_e<CB>();
-  constexpr int NT = E <= kPassElemsLog ? kColsThreads : kPassThreadsWide;
+  constexpr int NT = E < kPassElemsLog ? kPassThreads : (E == kPassElemsLog ? kColsThreads : kPassThreadsWide);
   k_fwd_rows<E, NT, CB><<<rows_grid(a.level, false, grid), NT, rows_smem(E, CB), s>>>(a);
 }
 template <int QB>
@@ -470,7 +470,7 @@ cudaError_t cols_attr() {
 template <int CB>
 cudaError_t rows_attr() {
   constexpr int E = rows_e<CB>();
-  constexpr int NT = E <= kPassElemsLog ? kColsThreads : kPassThreadsWide;
+  constexpr int NT = E < kPassElemsLog ? kPassThreads : (E == kPassElemsLog ? kColsThreads : kPassThreadsWide);
   return cudaFuncSetAttribute(k_fwd_rows<E, NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)rows_smem(E, CB));
 }

@@ -47,8 +47,7 @@ constexpr int kWinThreads = 256;             // levels 13, 14: 16 or 32 points p
 //   22, then 2^(i-12) -- so that Q <= 2^11 and every cols CTA reads chunks of
 //   at least 4 consecutive samples.
 //   cols pass: 2^13 points per CTA (RC = 2^13 / Q chunk offsets), 2 CTAs/SM
-//   rows pass: 2^rows_elems_log(i) points per CTA (KC = 2^E / C residues):
-//   2^13 (2^14 for C = 2^14); the adjoint's C = 2^10 rows use 2^12.
+//   rows pass: 2^rows_elems_log(i) points per CTA (KC = 2^E / C residues).
 constexpr int kPassElemsLog = 13;
 constexpr int kPassThreads = 256;        // 2^13-point rows / adjoint cols CTAs
 constexpr int kColsThreads = 512;        // forward cols and 2^12-point adjoint rows CTAs (64 registers)
@@ -56,8 +55,11 @@ constexpr int kPassThreadsWide = 512;    // the 2^14-point rows CTA (level 26)
 __host__ __device__ constexpr int cols_log(int i, bool adj) {
   return (i - 1) - 11 > (adj ? 10 : 11) ? (i - 1) - 11 : (adj ? 10 : 11);
 }
-__host__ __device__ constexpr int rows_elems_log_c(int cb) { return cb <= 10 ? 12 : (cb > 13 ? cb : 13); }
-__host__ __device__ constexpr int rows_elems_log(int i, bool adj) { return rows_elems_log_c(cols_log(i, adj)); }
+// rows CTA size: 2^12 points for the adjoint's C = 2^10, else 2^13 (2^14 for C = 2^14)
+__host__ __device__ constexpr int rows_elems_log_c(int cb, bool adj) {
+  return (adj && cb <= 10) ? 12 : (cb > 13 ? cb : 13);
+}
+__host__ __device__ constexpr int rows_elems_log(int i, bool adj) { return rows_elems_log_c(cols_log(i, adj), adj); }
 // work items of a two-pass level, per window: one per cols CTA (2^(i-14));
 // a rows CTA of 2^E points takes 2^(E-13) items (E >= 13) or half an item
 __host__ __device__ constexpr int pass_items(int i) { return 1 << ((i - 1) - kPassElemsLog); }
