@@ -132,6 +132,22 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
 
   // ---- levels tl .. 5 through shared memory
   const TwQ tw{TQ, TLOG};
+  // the gradient pairs of one level, requested a level ahead: a level's
+  // requests are issued before the previous level's FFT and arrive during it
+  constexpr int ITER = T / 2 / NT;
+  float4 gv[ITER];
+  auto load_level = [&](int lv) MRDFT_INL {
+#pragma unroll
+    for (int q = 0; q < ITER; ++q) {
+      const int c = tid + q * NT;
+      if (c < (Tn >> 1)) {
+        const int e = c << 1;
+        const AdjTileSig& ts = TS[e >> tl];
+        gv[q] = __ldcs(reinterpret_cast<const float4*>(a.gy + ts.g_base + ((int64_t)(lv - 1) << ts.m) + (e & ((1 << tl) - 1))));
+      }
+    }
+  };
+  load_level(tl);
   // one specialised FFT per level (compile-time lengths), top level first
   static_for<0, TLOG - 4>([&](auto J) MRDFT_INL {
     constexpr int i = TLOG - decltype(J)::value;
@@ -145,19 +161,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     }
     const float2* Ein = E[(i + 1) & 1];
     float2* Eout = E[i & 1];
-    // G_i = g_i + P_i: even half -> Eout, conj(odd half) -> Z; every gradient
-    // pair of the thread is requested before the first is used
-    constexpr int ITER = T / 2 / NT;
-    float4 gv[ITER];
-#pragma unroll
-    for (int q = 0; q < ITER; ++q) {
-      const int c = tid + q * NT;
-      if (c < (Tn >> 1)) {
-        const int e = c << 1;
-        const AdjTileSig& ts = TS[e >> tl];
-        gv[q] = __ldcs(reinterpret_cast<const float4*>(a.gy + ts.g_base + ((int64_t)(i - 1) << ts.m) + (e & ((1 << tl) - 1))));
-      }
-    }
+    // G_i = g_i + P_i: even half -> Eout, conj(odd half) -> Z
 #pragma unroll
     for (int q = 0; q < ITER; ++q) {
       const int c = tid + q * NT;
@@ -178,6 +182,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
       Z[stg<SA, 0>(w * h + (k >> 1))] = make_float2(g.z + p.z, -(g.w + p.w));
     }
     __syncthreads();
+    if constexpr (i > 5) load_level(i - 1);
     auto src = [&](int b, int n) MRDFT_INL -> float2 { return Z[stg<SA, 0>((b << (i - 1)) + n)]; };
     auto sink = [&](int, int b, int n, float2 v) MRDFT_INL {
       const float2 c = cmulc(conjf2(v), twq_l(tw, i, n));  // conj(w^n) zb[n]
