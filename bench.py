@@ -256,6 +256,7 @@ def main():
     ap.add_argument("--workload", default="single_16m")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cufft", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -416,6 +417,36 @@ def main():
     step_frac = alg_bytes / (ms_fwd * 1e-3) / 1e9 / peak
     step_frac_adj = alg_bytes / (ms_adj * 1e-3) / 1e9 / peak
 
+    # comparison: the method of computing every level separately (one batched
+    # cuFFT of all windows per level, through torch.fft) into the same output
+    cufft = None
+    if not args.no_cufft:
+        def per_level_fft():
+            xs = xt.to(torch.complex64) if real_input else xt
+            if len(set(lengths)) == 1:
+                n = lengths[0]
+                m = log2i(n)
+                xv = xs.view(len(lengths), n)
+                yv = y.view(len(lengths), m, n)
+                for i in range(1, m + 1):
+                    torch.fft.fft(xv.view(len(lengths), n >> i, 1 << i),
+                                  out=yv[:, i - 1, :].view(len(lengths), n >> i, 1 << i))
+            else:
+                yo = 0
+                xo = 0
+                for n in lengths:
+                    m = log2i(n)
+                    for i in range(1, m + 1):
+                        torch.fft.fft(xs[xo:xo + n].view(-1, 1 << i), out=y[yo + (i - 1) * n:yo + i * n].view(-1, 1 << i))
+                    xo += n
+                    yo += m * n
+        ksteps = max(3, min(args.steps, 20))
+        ms_fft = timed(per_level_fft, ksteps, 3)
+        cufft = {"ms_per_step": round(ms_fft, 4), "value": round(total_samples / (ms_fft * 1e-3) / 1e9, 4),
+                 "unit": "Gsamples/s", "mrdft_speedup": round(ms_fft / ms_fwd, 3),
+                 "what": "every level computed separately: one batched cuFFT (torch.fft.fft) of all windows per level, "
+                         "written into the same output layout"}
+
     # end to end through the C ABI with host buffers (H2D + transform + D2H)
     e2e = None
     if not args.no_e2e:
@@ -460,6 +491,7 @@ def main():
             "adjoint": {"value": round(value_adj, 4), "unit": "Gsamples/s", "ms_per_step": round(ms_adj, 4),
                         "hbm_frac_step": round(step_frac_adj, 4), "roofline": roof_adj},
             "e2e": e2e,
+            "per_level_cufft": cufft,
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": int(args.steps * info["fwd_launches"]),

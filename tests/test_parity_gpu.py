@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 from paper_1507_02525_gb300 import _lib, api, inputs  # noqa: E402
 
-from tests._parity import check_adjoint, check_forward_levels  # noqa: E402
+from tests._parity import ABS_FRAC, REL_PER_LEVEL, check_adjoint, check_forward_levels  # noqa: E402
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -357,3 +357,20 @@ def test_autograd_real_input(oracle):
         Yr = oracle.forward(x[s].astype(np.complex128))
         ref = oracle.adjoint(2 * Yr).real
         np.testing.assert_allclose(g[s], ref, rtol=0, atol=1e-5 * np.abs(ref).max())
+
+
+@pytest.mark.parametrize("B,m", [(1, 16), (4, 13)])
+def test_matches_per_level_cufft(B, m):
+    """Every level equals the batched FFT of its windows (cuFFT through torch.fft),
+    within the same FP32 tolerance: an independent cross-check of the layout."""
+    n = 1 << m
+    x = torch.from_numpy(inputs.complex_signals(B, n, seed=77 + m)).cuda()
+    y = api.mrdft(x)
+    torch.cuda.synchronize()
+    xn = float(torch.linalg.vector_norm(x.cpu().to(torch.complex128)))
+    for i in range(1, m + 1):
+        ref = torch.fft.fft(x.view(B, n >> i, 1 << i)).reshape(B, n).cpu().to(torch.complex128)
+        got = y[:, i - 1, :].cpu().to(torch.complex128)
+        rel = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
+        assert rel <= 2 * REL_PER_LEVEL * i, (i, rel)
+        assert float((got - ref).abs().max()) <= 2 * ABS_FRAC * xn
