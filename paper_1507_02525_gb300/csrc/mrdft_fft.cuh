@@ -72,20 +72,23 @@ __device__ __forceinline__ float2 twq(const TwQ& t, int e) {
 // w_{2^l}^e for l <= TB
 __device__ __forceinline__ float2 twq_l(const TwQ& t, int l, int e) { return twq(t, e << (t.TB - l)); }
 
-// w^(k * step), k = 0 .. R-1, from log2(R) table entries (w^step, w^2step,
-// w^4step) and products of them (at most two extra roundings).
+// w^(k * step), k = 0 .. R-1, from one table entry (w^step) and products of
+// it (at most four extra roundings, far inside the FP32 error budget): one
+// lookup instead of log2(R) keeps the table-index and quadrant arithmetic off
+// the critical path of every butterfly group.
+__device__ __forceinline__ float2 csq(float2 a) { return make_float2(fmaf(a.x, a.x, -a.y * a.y), 2.f * a.x * a.y); }
 template <int R>
 __device__ __forceinline__ void twiddle_set(const TwQ& tw, int step, float2 (&w)[R]) {
   w[0] = make_float2(1.f, 0.f);
   if constexpr (R >= 2) w[1] = twq(tw, step);
   if constexpr (R >= 4) {
-    w[2] = twq(tw, 2 * step);
+    w[2] = csq(w[1]);
     w[3] = cmul(w[1], w[2]);
   }
   if constexpr (R >= 8) {
-    w[4] = twq(tw, 4 * step);
+    w[4] = csq(w[2]);
     w[5] = cmul(w[4], w[1]);
-    w[6] = cmul(w[4], w[2]);
+    w[6] = csq(w[3]);
     w[7] = cmul(w[4], w[3]);
   }
 }
