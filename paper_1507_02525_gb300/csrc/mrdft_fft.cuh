@@ -118,7 +118,8 @@ __device__ __forceinline__ int drev8(int v, int d) {
 // in place; PTS bounds the points per thread (NT * PTS >= points per pass).
 constexpr int kPreNone = 0, kPreBarrier = 1, kPreGroup = 2, kPreHalf = 3;
 
-template <int RB, int NT, int PTS, bool SEQ_MINOR, bool FIRST, bool LAST, int PRE, int ZS, class Src, class Pre, class Sink>
+template <int RB, int NT, int PTS, bool SEQ_MINOR, bool FIRST, bool LAST, int PRE, int ZS, bool GSRC, class Src,
+          class Pre, class Sink>
 __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq_log, int SH, int P, const TwQ& tw,
                                         Src&& src, Pre&& pre, Sink&& sink) {
   constexpr int R = 1 << RB;
@@ -142,8 +143,12 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
       if constexpr (FIRST) {
         // position R g + r holds natural index drev8(g) + (L / R) r
         const int n0 = drev8(g, P - 1);
+        if constexpr (GSRC) {
+          src(b, n0, LRB, v[j], IC<RB>{});  // all R inputs n0 + (L / R) r at once
+        } else {
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[j][r] = src(b, n0 + (r << LRB));
+          for (int r = 0; r < R; ++r) v[j][r] = src(b, n0 + (r << LRB));
+        }
       } else {
         const int a0 = SEQ_MINOR ? (((g << RB) << nseq_log) + b) : ((b << LB) + (g << RB));
 #pragma unroll
@@ -205,8 +210,11 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
 // (LBMIN <= LB <= LBMAX, LB >= 1).  Starts with a barrier-free read of src,
 // ends after the sink; synchronises internally.  The caller synchronises
 // before reusing Z or reading what the sink wrote.
-//   src(b, n) -> float2;  pre(slot, b, k) (PRE != kPreNone);  sink(slot, b, k, v).
-template <int LBMIN, int LBMAX, int NT, int PTS, bool SEQ_MINOR, int PRE, int ZS = 0, class Src, class Pre, class Sink>
+//   src(b, n) -> float2, or with GSRC src(b, n0, LRB, float2 (&v)[R], IC<RB>)
+//   filling the R first-pass inputs n0 + (r << LRB) of a group at once;
+//   pre(slot, b, k) (PRE != kPreNone);  sink(slot, b, k, v).
+template <int LBMIN, int LBMAX, int NT, int PTS, bool SEQ_MINOR, int PRE, int ZS = 0, bool GSRC = false, class Src,
+          class Pre, class Sink>
 __device__ __forceinline__ void cg_fft(float2* __restrict__ Z, int LB, int nseq_log, const TwQ& tw, Src&& src,
                                        Pre&& pre, Sink&& sink) {
   const int P = (LB + 2) / 3;
@@ -216,7 +224,7 @@ __device__ __forceinline__ void cg_fft(float2* __restrict__ Z, int LB, int nseq_
       constexpr int rb = decltype(RR)::value;
       if constexpr (rb >= LBMIN && rb <= LBMAX)
         if (r0 == rb)
-          cg_pass<rb, NT, PTS, SEQ_MINOR, true, true, PRE, ZS>(Z, LB, nseq_log, LB, 1, tw, src, pre, sink);
+          cg_pass<rb, NT, PTS, SEQ_MINOR, true, true, PRE, ZS, GSRC>(Z, LB, nseq_log, LB, 1, tw, src, pre, sink);
     });
     return;
   }
@@ -224,15 +232,15 @@ __device__ __forceinline__ void cg_fft(float2* __restrict__ Z, int LB, int nseq_
     static_for<1, 4>([&](auto RR) MRDFT_INL {
       constexpr int rb = decltype(RR)::value;
       if (r0 == rb)
-        cg_pass<rb, NT, PTS, SEQ_MINOR, true, false, kPreNone, ZS>(Z, LB, nseq_log, 3 * (P - 1), P, tw, src, pre, sink);
+        cg_pass<rb, NT, PTS, SEQ_MINOR, true, false, kPreNone, ZS, GSRC>(Z, LB, nseq_log, 3 * (P - 1), P, tw, src, pre, sink);
     });
 #pragma unroll 1
     for (int p = P - 2; p >= 1; --p) {
       __syncthreads();
-      cg_pass<3, NT, PTS, SEQ_MINOR, false, false, kPreNone, ZS>(Z, LB, nseq_log, 3 * p, P, tw, src, pre, sink);
+      cg_pass<3, NT, PTS, SEQ_MINOR, false, false, kPreNone, ZS, false>(Z, LB, nseq_log, 3 * p, P, tw, src, pre, sink);
     }
     __syncthreads();
-    cg_pass<3, NT, PTS, SEQ_MINOR, false, true, PRE, ZS>(Z, LB, nseq_log, 0, P, tw, src, pre, sink);
+    cg_pass<3, NT, PTS, SEQ_MINOR, false, true, PRE, ZS, false>(Z, LB, nseq_log, 0, P, tw, src, pre, sink);
   }
 }
 

@@ -172,9 +172,17 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
     float2* ylev = a.y + TS[0].out_base + ((int64_t)(i - 1) << TS[0].m);  // single-signal tile
     const bool l2keep = i == tl && TS[0].m > tl;  // re-read as children of level tl+1
     float2 ev[8];
-    auto src = [&](int b, int n) MRDFT_INL -> float2 {
+    // V (Eq. 3) and D for a first-pass group: n = n0 + r 2^LRB, so
+    // w_{2^i}^n = w_{2^i}^n0 w_{2R}^r with the second factor a constant
+    auto src = [&](int b, int n0, int LRB, auto& v, auto RBc) MRDFT_INL {
+      constexpr int R = 1 << decltype(RBc)::value;
       const int base = b << i;
-      return cmul(csub(X[swz128(base + n)], X[swz128(base + h + n)]), twq_l(tw, i, n));
+      const float2 w0 = twq_l(tw, i, n0);
+      static_for<0, R>([&](auto RR) MRDFT_INL {
+        constexpr int r = decltype(RR)::value;
+        const int n = n0 + (r << LRB);
+        v[r] = cmul_ct<2 * R, r>(cmul(csub(X[swz128(base + n)], X[swz128(base + h + n)]), w0));
+      });
     };
     auto pre = [&](int slot, int b, int k) MRDFT_INL {
       const int base = b << i;
@@ -194,7 +202,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
       if (l2keep) __stcg(dst, v);
       else __stcs(dst, v);
     };
-    cg_fft<i - 1, i - 1, NT, 8, false, true>(Z, i - 1, tn_log - i, tw, src, pre, sink);
+    cg_fft<i - 1, i - 1, NT, 8, false, true, 0, true>(Z, i - 1, tn_log - i, tw, src, pre, sink);
     __syncthreads();
   });
 }
@@ -250,9 +258,18 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_fwd_window(const FwdArgs a) 
   __syncthreads();
   const TwQ tw{TQ, 13};
   // V (Eq. 3) and D: z[n] = (a[n] - b[n]) w_{2^i}^n, loads issued 8 at a time,
-  // z staged in the XOR layout that the first FFT pass reads digit-reversed
-#pragma unroll 1
-  for (int t0 = 0; t0 < PTS; t0 += 8) {
+  // z staged in the XOR layout that the first FFT pass reads digit-reversed;
+  // n = tid + 256 t, so w_{2^i}^n = w_{2^i}^tid w_{2^(i-8)}^t (a constant)
+  static_assert(NT == 256, "twiddle split assumes 256 threads");
+  float2 wt;
+  if constexpr (i <= 13) {
+    wt = twq_l(tw, i, threadIdx.x);
+  } else {
+    wt = twq(tw, threadIdx.x >> 1);
+    if (threadIdx.x & 1) wt = cmul(wt, w1);
+  }
+  static_for<0, PTS / 8>([&](auto T0) MRDFT_INL {
+    constexpr int t0 = decltype(T0)::value * 8;
     float2 xa[8], xb[8];
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -260,19 +277,12 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_fwd_window(const FwdArgs a) 
       xa[t] = load_x1(a, xs + n);
       xb[t] = load_x1(a, xs + h + n);
     }
-#pragma unroll
-    for (int t = 0; t < 8; ++t) {
+    static_for<0, 8>([&](auto TT) MRDFT_INL {
+      constexpr int t = decltype(TT)::value;
       const int n = threadIdx.x + (t0 + t) * NT;
-      float2 w;
-      if constexpr (i <= 13) {
-        w = twq_l(tw, i, n);
-      } else {
-        w = twq(tw, n >> 1);
-        if (n & 1) w = cmul(w, w1);
-      }
-      Z[stg<SA, SB>(n)] = cmul(csub(xa[t], xb[t]), w);
-    }
-  }
+      Z[stg<SA, SB>(n)] = cmul_ct<(1 << (i - 8)), t0 + t>(cmul(csub(xa[t], xb[t]), wt));
+    });
+  });
   __syncthreads();
   const bool reread = sd.m > i;  // children of the next level: keep in L2
   float2 ea[PTS], eb[PTS];
