@@ -131,8 +131,21 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
     const int64_t t0 = (int64_t)it.tile << tl;
     TS[tid] = TileSig{sd.in_off + t0, sd.out_off + t0, sd.m, 0};
   }
-  load_twq<NT>(TQ, TLOG, a.tw);
   __syncthreads();
+  // a tile that will run about one wave later (2 CTAs on each of ~152 SMs):
+  // start moving its x into L2 now, so that its staging is served from L2
+  if (tid == 0) {
+    const int fut = item + 2 * 152;
+    if (fut < a.nitems) {
+      const TileItem fi = reinterpret_cast<const TileItem*>(a.items)[fut];
+      if (fi.nsig == 1) {
+        const SigDesc fs = a.sigs[a.sig_ids[fi.sig_list]];
+        const int es = a.in_real ? 4 : 8;
+        const char* p = reinterpret_cast<const char*>(a.x) + (fs.in_off + ((int64_t)fi.tile << fi.tlog)) * es;
+        if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) prefetch_l2_bulk(p, (uint32_t)(es << fi.tlog));
+      }
+    }
+  }
 
   // ---- stage the tile of x (P^(1): x is read once and reused per level)
   if (!a.in_real) {
@@ -142,8 +155,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
       const int e = c << 1;
       cp_async16(X + swz128(e), xg + TS[e >> tl].in_base + (e & ((1 << tl) - 1)));
     }
+    load_twq<NT>(TQ, TLOG, a.tw);
     cp_async_wait_all();
   } else {
+    load_twq<NT>(TQ, TLOG, a.tw);
 #pragma unroll 4
     for (int c = tid; c < (Tn >> 1); c += NT) {
       const int e = c << 1;
