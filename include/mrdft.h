@@ -158,6 +158,23 @@ mrdft_status mrdft_timing_read(mrdft_plan_t plan, int kind, double* ms, int64_t*
                                int64_t* bytes);
 
 /*
+ * mrdft_loss_grad -- one fused loss-and-gradient step for fitting the
+ * multiresolution spectra to targets T (same layout and type as y):
+ *     L = sum_i 2^-i || Y^(i) - T^(i) ||^2,   Y = MrDFT(x)  (Sec. 2, Eq. 1),
+ *     gx = dL/dx* = adjoint(g),  g^(i) = 2^(1-i) (Y^(i) - T^(i)),
+ * where the adjoint is the conjugate transpose of Eq. 1 (as mrdft_adjoint).
+ * Writes Y to y, the gradient to gx (complex64; for MRDFT_R32 plans the
+ * gradient with respect to the real input is Re(gx)) and, when loss is not
+ * NULL, L to the device double *loss.  The adjoint reads Y and T directly:
+ * g is never materialised.  All pointers are device pointers owned by the
+ * caller (x, t, y, gx 16-byte aligned, loss 8-byte aligned); asynchronous on
+ * the stream.  The loss is summed with device atomics, so its last bits may
+ * differ between calls; Y and gx are deterministic.
+ */
+mrdft_status mrdft_loss_grad(mrdft_plan_t plan, const void* x, const void* t, void* y, void* gx, double* loss,
+                             mrdft_stream_t stream);
+
+/*
  * mrdft_forward_noalloc -- forward MrDFT of ONE complex64 signal of length n
  * (a power of two, 2 <= n <= 2^MRDFT_NOALLOC_MAX_LOG) without any plan and
  * without allocating: the paper has no counterpart; this entry point exists

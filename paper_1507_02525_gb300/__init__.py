@@ -6,7 +6,7 @@ Low level: ``paper_1507_02525_gb300._lib.Plan`` wraps the C ABI of include/mrdft
 Importing the package does not load CUDA; the library loads on first use.
 """
 
-__all__ = ["mrdft", "mrdft_adjoint", "mrdft_ragged", "mrdft_ragged_adjoint", "MrDFT", "get_plan"]
+__all__ = ["mrdft", "mrdft_adjoint", "mrdft_loss_grad", "mrdft_ragged", "mrdft_ragged_adjoint", "MrDFT", "get_plan"]
 
 
 def __getattr__(name):

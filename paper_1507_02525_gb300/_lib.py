@@ -30,8 +30,8 @@ STATUS_NAMES = {0: "MRDFT_OK", 1: "MRDFT_EINVAL", 2: "MRDFT_ENOMEM", 3: "MRDFT_E
 # every entry point declared in include/mrdft.h
 EXPORTS = ("mrdft_plan", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
            "mrdft_adjoint", "mrdft_forward_host", "mrdft_status_poll", "mrdft_last_error",
-           "mrdft_plan_info", "mrdft_timing_enable", "mrdft_timing_read", "mrdft_forward_noalloc",
-           "mrdft_destroy")
+           "mrdft_plan_info", "mrdft_timing_enable", "mrdft_timing_read", "mrdft_loss_grad",
+           "mrdft_forward_noalloc", "mrdft_destroy")
 NOALLOC_MAX_LOG = 16
 
 KINDS = ("fwd_tile", "fwd_tiny", "fwd_window", "fwd_cols", "fwd_rows",
@@ -77,13 +77,14 @@ def load(build_if_missing: bool = True):
         lib.mrdft_timing_enable.argtypes = [vp, i32]
         lib.mrdft_timing_read.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_double),
                                           ctypes.POINTER(i64), ctypes.POINTER(i64)]
+        lib.mrdft_loss_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.mrdft_forward_noalloc.argtypes = [vp, vp, i64, vp]
         lib.mrdft_forward_noalloc.restype = ctypes.c_int
         lib.mrdft_destroy.argtypes = [vp]
         lib.mrdft_destroy.restype = None
         for name in ("mrdft_plan", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
                      "mrdft_adjoint", "mrdft_forward_host", "mrdft_status_poll", "mrdft_plan_info",
-                     "mrdft_timing_enable", "mrdft_timing_read"):
+                     "mrdft_timing_enable", "mrdft_timing_read", "mrdft_loss_grad"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -145,6 +146,13 @@ class Plan:
     def adjoint(self, gy_ptr: int, gx_ptr: int, stream: int = 0) -> None:
         check(self._lib.mrdft_adjoint(self._h, ctypes.c_void_p(gy_ptr), ctypes.c_void_p(gx_ptr),
                                       ctypes.c_void_p(stream)), self._h)
+
+    def loss_grad(self, x_ptr: int, t_ptr: int, y_ptr: int, gx_ptr: int, loss_ptr: int, stream: int = 0) -> None:
+        """mrdft_loss_grad: Y = MrDFT(x), L = sum_i 2^-i |Y_i - T_i|^2 into the
+        device double at loss_ptr (0: not computed), gx = dL/dx*."""
+        check(self._lib.mrdft_loss_grad(self._h, ctypes.c_void_p(x_ptr), ctypes.c_void_p(t_ptr),
+                                        ctypes.c_void_p(y_ptr), ctypes.c_void_p(gx_ptr),
+                                        ctypes.c_void_p(loss_ptr or None), ctypes.c_void_p(stream)), self._h)
 
     def forward_host(self, x_host_ptr: int, y_host_ptr: int, stream: int = 0) -> None:
         check(self._lib.mrdft_forward_host(self._h, ctypes.c_void_p(x_host_ptr),

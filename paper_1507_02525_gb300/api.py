@@ -89,6 +89,37 @@ def mrdft_adjoint(gy: torch.Tensor, graph: bool = False) -> torch.Tensor:
     return gx[0] if squeeze else gx
 
 
+def mrdft_loss_grad(x: torch.Tensor, t: torch.Tensor, graph: bool = False):
+    """Fused loss and gradient for fitting the level spectra to targets t:
+    L = sum_i 2^-i ||Y^(i) - T^(i)||^2 with Y = MrDFT(x).
+
+    x: [B, N] (or [N]) complex64 or float32 CUDA; t: [B, m, N] (or [m, N])
+    complex64.  Returns (L as a 0-d float64 CUDA tensor, Y [B, m, N], gx):
+    gx is dL/dx* (complex64 [B, N]); for real x the gradient is its real part
+    (returned as float32).  The adjoint reads Y and T directly.
+    """
+    x = _check_input(x)
+    squeeze = x.dim() == 1
+    xb = x.unsqueeze(0) if squeeze else x
+    B, N = xb.shape
+    m = _log2(N)
+    if not t.is_cuda or t.dtype != torch.complex64:
+        raise TypeError("mrdft_loss_grad: t must be a complex64 CUDA tensor")
+    tb = (t.unsqueeze(0) if squeeze else t).contiguous()
+    if tuple(tb.shape) != (B, m, N):
+        raise ValueError(f"mrdft_loss_grad: t must have shape {(B, m, N)}")
+    real = xb.dtype == torch.float32
+    plan = get_plan([N], B, real, graph, xb.device)
+    y = torch.empty((B, m, N), dtype=torch.complex64, device=xb.device)
+    gx = torch.empty((B, N), dtype=torch.complex64, device=xb.device)
+    loss = torch.zeros((), dtype=torch.float64, device=xb.device)
+    plan.loss_grad(xb.data_ptr(), tb.data_ptr(), y.data_ptr(), gx.data_ptr(), loss.data_ptr(), _stream_ptr())
+    g = gx.real.contiguous() if real else gx
+    if squeeze:
+        return loss, y[0], g[0]
+    return loss, y, g
+
+
 def mrdft_ragged(x: torch.Tensor, lengths, graph: bool = False) -> torch.Tensor:
     """Forward MrDFT of signals of uneven power-of-two lengths, concatenated in x.
 

@@ -33,10 +33,45 @@ struct AdjTileSig {
 };
 constexpr int kAdjMaxPack = kTile / 32;
 
+// Upstream gradient of a bin pair at p (a float4 inside gy) of level i: g
+// itself, or for the fused loss 2^(1-i) (Y - T), with 2^-i |Y - T|^2 added to
+// the thread's partial loss.
+template <bool FUSED>
+__device__ __forceinline__ float4 grad4(const AdjArgs& a, const float4* p, int i, float& lsum) {
+  float4 v = __ldcs(p);
+  if constexpr (FUSED) {
+    const float4 t = __ldcs(reinterpret_cast<const float4*>(a.t) + (p - reinterpret_cast<const float4*>(a.gy)));
+    const float sc = ldexpf(1.f, -i);
+    const float dx = v.x - t.x, dy = v.y - t.y, dz = v.z - t.z, dw = v.w - t.w;
+    lsum = fmaf(sc, dx * dx + dy * dy + dz * dz + dw * dw, lsum);
+    const float g = 2.f * sc;
+    v = make_float4(g * dx, g * dy, g * dz, g * dw);
+  }
+  return v;
+}
+// Adds the block's partial losses to *loss (one atomic per block); every
+// thread of the block must call it.
+template <bool FUSED>
+__device__ __forceinline__ void loss_flush(const AdjArgs& a, float lsum) {
+  if constexpr (!FUSED) return;
+  if (a.loss == nullptr) return;
+  __shared__ float red[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = lsum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float s = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+    atomicAdd(a.loss, (double)s);
+  }
+}
+
 // Levels 4..1 of one 16-position chunk (a level-4 window) in registers.
 // P = the level-5 parent's even bins for this window, acc = x_bar so far.
+template <bool FUSED>
 __device__ __forceinline__ void adj_chunk_levels_4_1(const AdjArgs& a, const AdjTileSig& ts, int off,
-                                                     float2 (&P)[16], float2 (&acc)[16]) {
+                                                     float2 (&P)[16], float2 (&acc)[16], float& lsum) {
   const float2* gl = a.gy + ts.g_base + off;
   const int64_t lstride = (int64_t)1 << ts.m;
   static_for<0, 4>([&](auto JJ) MRDFT_INL {
@@ -46,7 +81,7 @@ __device__ __forceinline__ void adj_chunk_levels_4_1(const AdjArgs& a, const Adj
     const float4* g4 = reinterpret_cast<const float4*>(gl + (j - 1) * lstride);
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
-      const float4 v = __ldcs(g4 + q);
+      const float4 v = grad4<FUSED>(a, g4 + q, j, lsum);
       G[2 * q] = make_float2(v.x, v.y);
       G[2 * q + 1] = make_float2(v.z, v.w);
     }
@@ -86,7 +121,7 @@ __device__ __forceinline__ void adj_chunk_levels_4_1(const AdjArgs& a, const Adj
   });
 }
 
-template <int TLOG, int NT>
+template <int TLOG, int NT, bool FUSED>
 __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArgs a) {
   constexpr int T = 1 << TLOG;
   static_assert(T == 16 * NT, "tile = 16 samples per thread");
@@ -136,6 +171,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
   // requests are issued before the previous level's FFT and arrive during it
   constexpr int ITER = T / 2 / NT;
   float4 gv[ITER];
+  float lsum = 0.f;  // fused loss: this thread's share
   auto load_level = [&](int lv) MRDFT_INL {
 #pragma unroll
     for (int q = 0; q < ITER; ++q) {
@@ -143,7 +179,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
       if (c < (Tn >> 1)) {
         const int e = c << 1;
         const AdjTileSig& ts = TS[e >> tl];
-        gv[q] = __ldcs(reinterpret_cast<const float4*>(a.gy + ts.g_base + ((int64_t)(lv - 1) << ts.m) + (e & ((1 << tl) - 1))));
+        gv[q] = grad4<FUSED>(a, reinterpret_cast<const float4*>(a.gy + ts.g_base + ((int64_t)(lv - 1) << ts.m) + (e & ((1 << tl) - 1))),
+                      lv, lsum);
       }
     }
   };
@@ -196,10 +233,9 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
   });
 
   // ---- levels 4 .. 1 in registers, one 16-position chunk per thread
-  {
-    const int chunk = tid;
-    const int e = chunk << 4;
-    if (e >= Tn) return;
+  const int chunk = tid;
+  const int e = chunk << 4;
+  if (e < Tn) {
     float2 P[16], acc[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
@@ -208,39 +244,52 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     }
     const AdjTileSig& ts = TS[e >> tl];
     const int off = e & ((1 << tl) - 1);
-    adj_chunk_levels_4_1(a, ts, off, P, acc);
+    adj_chunk_levels_4_1<FUSED>(a, ts, off, P, acc, lsum);
     float4* dst = reinterpret_cast<float4*>(a.gx + ts.x_base + off);
 #pragma unroll
     for (int q = 0; q < 8; ++q)
       __stcs(dst + q, make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y));
   }
+  loss_flush<FUSED>(a, lsum);
 }
 
 // ===================================================================== tiny
 
 // Signals with N <= 16: conjugate transpose of Eq. 1 term by term.
+template <bool FUSED>
 __global__ void k_adj_tiny(const AdjArgs a) {
   const SigDesc sd = a.sigs[a.sig_ids[blockIdx.x]];
   const int N = 1 << sd.m;
   const int n = threadIdx.x;
-  if (n >= N) return;
-  float2 acc = make_float2(0.f, 0.f);
-  for (int i = 1; i <= sd.m; ++i) {
-    const int L = 1 << i, w = n >> i, nl = n & (L - 1);
-    for (int k = 0; k < L; ++k) {
-      const float2 g = a.gy[sd.out_off + ((int64_t)(i - 1) << sd.m) + (w << i) + k];
-      acc = cadd(acc, cmulc(g, tw_small(a.tw, i, (nl * k) & (L - 1))));
+  float lsum = 0.f;
+  if (n < N) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int i = 1; i <= sd.m; ++i) {
+      const int L = 1 << i, w = n >> i, nl = n & (L - 1);
+      const float sc = ldexpf(1.f, -i);
+      for (int k = 0; k < L; ++k) {
+        const int64_t idx = sd.out_off + ((int64_t)(i - 1) << sd.m) + (w << i) + k;
+        float2 g = a.gy[idx];
+        if constexpr (FUSED) {  // fused loss: 2^(1-i) (Y - T); bin n's term counted by thread n
+          const float2 d = csub(g, a.t[idx]);
+          if (k == nl) lsum = fmaf(sc, d.x * d.x + d.y * d.y, lsum);
+          g = make_float2(2.f * sc * d.x, 2.f * sc * d.y);
+        }
+        acc = cadd(acc, cmulc(g, tw_small(a.tw, i, (nl * k) & (L - 1))));
+      }
     }
+    a.gx[sd.in_off + n] = acc;
   }
-  a.gx[sd.in_off + n] = acc;
+  loss_flush<FUSED>(a, lsum);
 }
 
 // =================================================================== window
 
 // Accumulated gradient of a bin pair (2k, 2k+1) of window w at level i:
 // upstream g plus the parent's propagated even bins (none at the top level).
-__device__ __forceinline__ float4 adj_G(const AdjArgs& a, const SigDesc& sd, int i, int64_t w, int64_t k2) {
-  float4 g = __ldcs(reinterpret_cast<const float4*>(a.gy + sd.out_off + ((int64_t)(i - 1) << sd.m) + (w << i) + k2));
+template <bool FUSED>
+__device__ __forceinline__ float4 adj_G(const AdjArgs& a, const SigDesc& sd, int i, int64_t w, int64_t k2, float& lsum) {
+  float4 g = grad4<FUSED>(a, reinterpret_cast<const float4*>(a.gy + sd.out_off + ((int64_t)(i - 1) << sd.m) + (w << i) + k2), i, lsum);
   if (sd.m > i) {
     const float4 p = __ldcg(reinterpret_cast<const float4*>(a.e_in + sd.aux_off + ((w >> 1) << i) + k2));
     g.x += p.x; g.y += p.y; g.z += p.z; g.w += p.w;
@@ -251,7 +300,7 @@ __device__ __forceinline__ float4 adj_G(const AdjArgs& a, const SigDesc& sd, int
 // One window of level i = LB + 1 per CTA: G = g + propagated even bins; even
 // half -> e_out; IDFT_h of the odd half; conj(w_{2^i}^n) times it added to
 // the accumulator at n and subtracted at h + n (accumulator read per group).
-template <int LB>
+template <int LB, bool FUSED>
 __global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) {
   constexpr int NT = kWinThreads;
   constexpr int h = 1 << LB;
@@ -272,11 +321,12 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) 
     prefetch_l2_bulk(acc + (threadIdx.x >> 1) * 2048 + (threadIdx.x & 1) * h, 2048 * sizeof(float2));
   load_twq<NT>(TQ, 13, a.tw);
   const float2 w1 = __ldg(&a.tw.tw13[1]);  // w_{2^14}
+  float lsum = 0.f;  // fused loss: this thread's share
 #pragma unroll 1
   for (int t0 = 0; t0 < PTS; t0 += 8) {
     float4 g[8];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) g[t] = adj_G(a, sd, i, w, 2 * (int64_t)(threadIdx.x + (t0 + t) * NT));
+    for (int t = 0; t < 8; ++t) g[t] = adj_G<FUSED>(a, sd, i, w, 2 * (int64_t)(threadIdx.x + (t0 + t) * NT), lsum);
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int k = threadIdx.x + (t0 + t) * NT;
@@ -312,6 +362,7 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) 
     }
   };
   cg_fft<LB, LB, NT, PTS, false, kPreGroup>(Z, LB, 0, tw, src, pre, sink);
+  loss_flush<FUSED>(a, lsum);
 }
 
 constexpr size_t adj_cols_smem(int E) {
@@ -331,7 +382,7 @@ constexpr int adj_rows_e() { return rows_elems_log_c(CB, true); }
 // rows: a CTA of 2^E points covers residues k2 in [k0, k0 + KC), KC = 2^E / C:
 //   odd-bin gradients at k = Q k1 + k2 -> IDFT_C over k1 -> times
 //   conj(w_h^(r k2)) -> scratch U[window][k2][r]; even bins -> e_out.
-template <int E, int NT, int CB>
+template <int E, int NT, int CB, bool FUSED>
 __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(const AdjArgs a) {
   constexpr int PTS = (1 << E) / NT;
   constexpr int KCB = E - CB, KC = 1 << KCB;
@@ -363,6 +414,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
   const int64_t w = it.window;
   const int k0 = blk << KCB;
   // gradient pairs (2k, 2k+1): a batch of loads is issued before any store
+  float lsum = 0.f;  // fused loss: this thread's share
 #pragma unroll 1
   for (int t0 = 0; t0 < PTS; t0 += 8) {
     float4 g[8];
@@ -370,7 +422,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
     for (int t = 0; t < 8; ++t) {
       const int e = threadIdx.x + (t0 + t) * NT;
       const int64_t k = ((int64_t)(e >> KCB) << QB) + k0 + (e & (KC - 1));
-      g[t] = adj_G(a, sd, i, w, 2 * k);
+      g[t] = adj_G<FUSED>(a, sd, i, w, 2 * k, lsum);
     }
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -400,6 +452,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
     __stcg(U + ((int64_t)(k0 + b) << CB) + r, cmulc(conjf2(v), t));
   };
   cg_fft<CB, CB, NT, PTS, false, kPreNone>(S, CB, KCB, tw, src, NoPre{}, sink);
+  loss_flush<FUSED>(a, lsum);
 }
 
 // cols: item (sig, window, c) covers chunk offsets r in [r0, r0 + RC),
@@ -480,7 +533,10 @@ template <int CB>
 void adj_rows_launch(const AdjArgs& a, int grid, cudaStream_t s) {
   constexpr int E = adj_rows_e<CB>();
   constexpr int NT = E < kPassElemsLog ? kColsThreads : (E == kPassElemsLog ? kPassThreads : kPassThreadsWide);
-  k_adj_rows<E, NT, CB><<<rows_grid(a.level, true, grid), NT, adj_rows_smem(E, CB), s>>>(a);
+  if (a.t)
+    k_adj_rows<E, NT, CB, true><<<rows_grid(a.level, true, grid), NT, adj_rows_smem(E, CB), s>>>(a);
+  else
+    k_adj_rows<E, NT, CB, false><<<rows_grid(a.level, true, grid), NT, adj_rows_smem(E, CB), s>>>(a);
 }
 template <int QB>
 cudaError_t adj_cols_attr() {
@@ -493,8 +549,12 @@ template <int CB>
 cudaError_t adj_rows_attr() {
   constexpr int E = adj_rows_e<CB>();
   constexpr int NT = E < kPassElemsLog ? kColsThreads : (E == kPassElemsLog ? kPassThreads : kPassThreadsWide);
-  return cudaFuncSetAttribute(k_adj_rows<E, NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)adj_rows_smem(E, CB));
+  cudaError_t e = cudaFuncSetAttribute(k_adj_rows<E, NT, CB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)adj_rows_smem(E, CB));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_rows<E, NT, CB, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)adj_rows_smem(E, CB));
+  return e;
 }
 
 // ================================================================ launchers
@@ -503,12 +563,19 @@ static constexpr size_t kAdjTileSmem =
     (size_t)(2 * kTile + kTile / 2 + twq_size(kTileLog)) * sizeof(float2) + kAdjMaxPack * sizeof(AdjTileSig);
 static constexpr size_t kAdjWinSmem = (size_t)((1 << kWinMaxLog) + twq_size(13)) * sizeof(float2);
 cudaError_t set_adj_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_adj_tile<kTileLog, kTileThreads>,
+  cudaError_t e = cudaFuncSetAttribute(k_adj_tile<kTileLog, kTileThreads, true>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjTileSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adj_window<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
+    e = cudaFuncSetAttribute(k_adj_tile<kTileLog, kTileThreads, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjTileSmem);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_adj_window<13>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
+    e = cudaFuncSetAttribute(k_adj_window<12, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_window<12, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_window<13, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_window<13, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
   static_for_host<4, 12>([&](auto Q) {
     if (e == cudaSuccess) e = adj_cols_attr<decltype(Q)::value>();
   });
@@ -519,18 +586,26 @@ cudaError_t set_adj_attributes() {
 }
 
 cudaError_t launch_adj_tile(const AdjArgs& a, int grid, cudaStream_t s) {
-  k_adj_tile<kTileLog, kTileThreads><<<grid, kTileThreads, kAdjTileSmem, s>>>(a);
+  if (a.t)
+    k_adj_tile<kTileLog, kTileThreads, true><<<grid, kTileThreads, kAdjTileSmem, s>>>(a);
+  else
+    k_adj_tile<kTileLog, kTileThreads, false><<<grid, kTileThreads, kAdjTileSmem, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_adj_tiny(const AdjArgs& a, int nsig_tiny, cudaStream_t s) {
-  k_adj_tiny<<<nsig_tiny, 32, 0, s>>>(a);
+  if (a.t)
+    k_adj_tiny<true><<<nsig_tiny, 32, 0, s>>>(a);
+  else
+    k_adj_tiny<false><<<nsig_tiny, 32, 0, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s) {
   if (a.level == 13)
-    k_adj_window<12><<<grid, kWinThreads, kAdjWinSmem, s>>>(a);
+    a.t ? k_adj_window<12, true><<<grid, kWinThreads, kAdjWinSmem, s>>>(a)
+        : k_adj_window<12, false><<<grid, kWinThreads, kAdjWinSmem, s>>>(a);
   else
-    k_adj_window<13><<<grid, kWinThreads, kAdjWinSmem, s>>>(a);
+    a.t ? k_adj_window<13, true><<<grid, kWinThreads, kAdjWinSmem, s>>>(a)
+        : k_adj_window<13, false><<<grid, kWinThreads, kAdjWinSmem, s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s) {

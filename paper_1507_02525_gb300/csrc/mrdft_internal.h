@@ -97,6 +97,11 @@ struct AdjArgs {
   int first;           // 1 when this is the top level (no e_in, acc written not added)
   Twiddles tw;
   int* status;
+  // fused loss gradient: when t != nullptr, gy holds the forward output Y and
+  // the upstream gradient of level i is 2^(1-i) (Y - T); sum_i 2^-i |Y - T|^2
+  // is added to *loss (which may be nullptr)
+  const float2* t;
+  double* loss;
 };
 
 // launchers (defined in the .cu files)

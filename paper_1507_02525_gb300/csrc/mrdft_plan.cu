@@ -57,10 +57,14 @@ struct GraphKey {
   const void* a;
   const void* b;
   cudaStream_t s;
+  const void* t;  // fused loss gradient: targets and loss accumulator
+  const void* l;
   bool operator<(const GraphKey& o) const {
     if (a != o.a) return a < o.a;
     if (b != o.b) return b < o.b;
-    return s < o.s;
+    if (s != o.s) return s < o.s;
+    if (t != o.t) return t < o.t;
+    return l < o.l;
   }
 };
 
@@ -112,6 +116,9 @@ struct mrdft_plan_s {
 
 
   std::map<GraphKey, cudaGraphExec_t> fwd_graphs, adj_graphs;
+  // adjoint launches of mrdft_loss_grad: targets and loss accumulator (else null)
+  const float2* cur_t = nullptr;
+  double* cur_loss = nullptr;
   std::string err = "no error";
 
   // optional per-kernel timing (events around every launch, no graph replay);
@@ -529,6 +536,8 @@ mrdft_status enqueue_adjoint(mrdft_plan_s* p, const void* gy, void* gx, cudaStre
   a.scratch = p->d_scratch;
   a.tw = twiddles(p);
   a.status = p->d_status;
+  a.t = p->cur_t;
+  a.loss = p->cur_loss;
   for (auto it = p->top.rbegin(); it != p->top.rend(); ++it) {
     mrdft_status r = launch_adj(p, a, *it, st);
     if (r != MRDFT_OK) return r;
@@ -558,7 +567,7 @@ mrdft_status run(mrdft_plan_s* p, std::map<GraphKey, cudaGraphExec_t>& cache, En
   MRDFT_CUDA(p, cudaGetDevice(&dev));
   if (dev != p->device) return fail(p, MRDFT_EINVAL, "plan used on a different device than it was created on");
   if (!(p->flags & MRDFT_FLAG_GRAPH) || p->timing) return fn(p, in, out, st);
-  const GraphKey key{in, out, st};
+  const GraphKey key{in, out, st, p->cur_t, p->cur_loss};
   auto found = cache.find(key);
   if (found == cache.end()) {
     cudaStream_t cap = st;
@@ -652,6 +661,26 @@ mrdft_status mrdft_adjoint(mrdft_plan_t p, const void* gy, void* gx, mrdft_strea
   if (!gy || !gx) return fail(p, MRDFT_EINVAL, "mrdft_adjoint: gy or gx is NULL");
   if (misaligned(gy) || misaligned(gx)) return fail(p, MRDFT_EINVAL, "mrdft_adjoint: gy and gx must be 16-byte aligned");
   return run(p, p->adj_graphs, enqueue_adjoint, gy, gx, reinterpret_cast<cudaStream_t>(stream));
+}
+
+mrdft_status mrdft_loss_grad(mrdft_plan_t p, const void* x, const void* t, void* y, void* gx, double* loss,
+                             mrdft_stream_t stream) {
+  if (!p) return fail(nullptr, MRDFT_EINVAL, "mrdft_loss_grad: plan is NULL");
+  if (!x || !t || !y || !gx) return fail(p, MRDFT_EINVAL, "mrdft_loss_grad: x, t, y or gx is NULL");
+  if (misaligned(x) || misaligned(t) || misaligned(y) || misaligned(gx))
+    return fail(p, MRDFT_EINVAL, "mrdft_loss_grad: buffers must be 16-byte aligned");
+  if (loss && (reinterpret_cast<uintptr_t>(loss) & 7) != 0)
+    return fail(p, MRDFT_EINVAL, "mrdft_loss_grad: loss must be 8-byte aligned");
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  mrdft_status s = run(p, p->fwd_graphs, enqueue_forward, x, y, st);
+  if (s != MRDFT_OK) return s;
+  if (loss) MRDFT_CUDA(p, cudaMemsetAsync(loss, 0, sizeof(double), st));
+  p->cur_t = reinterpret_cast<const float2*>(t);
+  p->cur_loss = loss;
+  s = run(p, p->adj_graphs, enqueue_adjoint, y, gx, st);
+  p->cur_t = nullptr;
+  p->cur_loss = nullptr;
+  return s;
 }
 
 mrdft_status mrdft_forward_host(mrdft_plan_t p, const void* x_host, void* y_host, mrdft_stream_t stream) {

@@ -374,3 +374,59 @@ def test_matches_per_level_cufft(B, m):
         rel = float(torch.linalg.vector_norm(got - ref) / torch.linalg.vector_norm(ref))
         assert rel <= 2 * REL_PER_LEVEL * i, (i, rel)
         assert float((got - ref).abs().max()) <= 2 * ABS_FRAC * xn
+
+
+@pytest.mark.parametrize("B,m,real", [(8, 3, False), (4, 12, False), (2, 17, False), (4, 15, True)])
+def test_fused_loss_grad(oracle, B, m, real):
+    """mrdft_loss_grad: Y, L = sum_i 2^-i ||Y_i - T_i||^2 and gx = adjoint of
+    2^(1-i) (Y_i - T_i) in one call, against the oracle (FP64 forward, residual,
+    adjoint) and against the unfused adjoint of the same residual."""
+    N = 1 << m
+    x = inputs.real_signals(B, N, seed=40 + m) if real else inputs.complex_signals(B, N, seed=40 + m)
+    T = inputs.targets(B, N, seed=50 + m)
+    xt = torch.from_numpy(x).cuda()
+    Tt = torch.from_numpy(T).cuda()
+    loss, y, g = api.mrdft_loss_grad(xt, Tt)
+    torch.cuda.synchronize()
+    wn = 2.0 ** -np.arange(1, m + 1)
+    ys = y.cpu().numpy()
+    gs = g.cpu().numpy()
+    L_ref = 0.0
+    for s in range(B):
+        xs = x[s].astype(np.complex128)
+        Yr = oracle.forward(xs)
+        check_forward_levels(ys[s], Yr, xs, f"signal {s}")
+        res = Yr - T[s].astype(np.complex128)
+        L_ref += float((wn[:, None] * np.abs(res) ** 2).sum())
+        gref = oracle.adjoint(2 * wn[:, None] * res)
+        if real:
+            gref = gref.real
+        rel = np.linalg.norm(gs[s] - gref) / np.linalg.norm(gref)
+        assert rel <= ADJ_REL_FUSED, f"signal {s}: gradient rel {rel:.3e}"
+    assert abs(float(loss) - L_ref) <= 1e-5 * L_ref, (float(loss), L_ref)
+    # unfused: the residual materialised, then the plain adjoint
+    w = torch.tensor(wn, dtype=torch.float32, device="cuda").view(1, m, 1)
+    gy = (2 * w * (y - Tt)).to(torch.complex64)
+    g2 = api.mrdft_adjoint(gy)
+    if real:
+        g2 = g2.real
+    d = (g2 - g).abs().max().item()
+    assert d <= 1e-5 * g2.abs().max().item()
+
+
+ADJ_REL_FUSED = 1e-5
+
+
+def test_fused_loss_grad_graph_and_repeat():
+    """The fused call under graph replay returns the same loss and gradient
+    every time (the loss accumulator is reset on every call)."""
+    B, m = 4, 16
+    N = 1 << m
+    xt = torch.from_numpy(inputs.complex_signals(B, N, seed=61)).cuda()
+    Tt = torch.from_numpy(inputs.targets(B, N, seed=62)).cuda()
+    l0, y0, g0 = api.mrdft_loss_grad(xt, Tt, graph=True)
+    for _ in range(3):
+        l1, y1, g1 = api.mrdft_loss_grad(xt, Tt, graph=True)
+        torch.cuda.synchronize()
+        assert torch.equal(y0, y1) and torch.equal(g0, g1)
+        assert abs(float(l1) - float(l0)) <= 1e-9 * abs(float(l0))
