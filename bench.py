@@ -257,6 +257,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
+    ap.add_argument("--no-train", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -447,6 +448,37 @@ def main():
                  "what": "every level computed separately: one batched cuFFT (torch.fft.fft) of all windows per level, "
                          "written into the same output layout"}
 
+    # training step for fitting the level spectra to targets T (uniform batches):
+    # L = sum_i 2^-i ||Y_i - T_i||^2 and dL/dx*, fused (mrdft_loss_grad: the
+    # adjoint reads Y and T) against forward + residual in torch + adjoint
+    train = None
+    if not args.no_train and len(set(lengths)) == 1:
+        n = lengths[0]
+        m = log2i(n)
+        B = len(lengths)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(5 + 1000 * rank)
+        tt = torch.randn((B, m, n), dtype=torch.complex64, device=dev, generator=gen)
+        loss_t = torch.zeros((), dtype=torch.float64, device=dev)
+        wlev = torch.tensor([2.0 ** -(i + 1) for i in range(m)], dtype=torch.float32, device=dev).view(1, m, 1)
+
+        def fused():
+            plan.loss_grad(xt.data_ptr(), tt.data_ptr(), y.data_ptr(), gx.data_ptr(), loss_t.data_ptr(), sp)
+
+        def unfused():
+            plan.forward(xt.data_ptr(), y.data_ptr(), sp)
+            gy = (2.0 * wlev) * (y.view(B, m, n) - tt)
+            plan.adjoint(gy.data_ptr(), gx.data_ptr(), sp)
+
+        ksteps = max(3, min(args.steps, 20))
+        ms_fused = timed(fused, ksteps, 3)
+        ms_unfused = timed(unfused, ksteps, 3)
+        train = {"fused_ms": round(ms_fused, 4), "unfused_ms": round(ms_unfused, 4),
+                 "speedup": round(ms_unfused / ms_fused, 3),
+                 "what": "L = sum_i 2^-i ||Y_i - T_i||^2 and dL/dx*: mrdft_loss_grad vs mrdft_forward + "
+                         "torch residual + mrdft_adjoint; T ~ CN(0,1) seeded on the device"}
+        del tt
+
     # end to end through the C ABI with host buffers (H2D + transform + D2H)
     e2e = None
     if not args.no_e2e:
@@ -492,6 +524,7 @@ def main():
                         "hbm_frac_step": round(step_frac_adj, 4), "roofline": roof_adj},
             "e2e": e2e,
             "per_level_cufft": cufft,
+            "train_step": train,
             "cpu_baseline": cpu,
             "clocks": clk,
             "gpu_launches": int(args.steps * info["fwd_launches"]),
