@@ -12,6 +12,9 @@
 //     even-bin propagation to the next level in `e_out` (N/2 per signal),
 //     time-domain contributions accumulated in `acc` (N per signal).
 //   k_adj_tile : levels tlog..1 of a tile, adds `acc`, writes x_bar.
+// Every gradient-reading kernel has a FUSED variant (mrdft_loss_grad): gy then
+// holds Y, the upstream gradient of level i is 2^(1-i) (Y - T) computed on the
+// fly, and the block's share of sum_i 2^-i |Y - T|^2 goes to one atomic add.
 #include <cuda_runtime.h>
 
 #include "mrdft_fft.cuh"

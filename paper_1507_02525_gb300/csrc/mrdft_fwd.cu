@@ -7,14 +7,14 @@
 // and level 1 is (x0 + x1, x0 - x1) (A^(1)).  The permutation Gamma is folded
 // into the store index (bins are written in natural order).
 //
-//   k_fwd_tile   levels 1..tlog of a 2^tlog-sample tile in shared memory:
-//                levels 1..5 per thread in registers (32 samples per thread),
-//                levels 6..12 through the shared-memory FFT engine.
+//   k_fwd_tile   levels 1..tlog (tlog <= 12) of a tile in shared memory:
+//                levels 1..4 per thread in registers (16 samples per thread),
+//                levels 5..12 through the shared-memory FFT engine.
 //   k_fwd_tiny   signals of length 2, 4, 8, 16 (Eq. 1 term by term).
-//   k_fwd_window one level i (2^12 < 2^i <= 2^14) of one window per CTA.
-//   k_fwd_cols / k_fwd_rows  one level i > 14 in two passes: DFT_h with
-//                h = Q * 4096 split as a length-Q DFT across 4096-sample
-//                chunks (cols) and a length-4096 DFT per output residue (rows).
+//   k_fwd_window one level (13 or 14) of one window per CTA.
+//   k_fwd_cols / k_fwd_rows  one level i >= 15 in two passes: DFT_h with
+//                h = Q * C split as a length-Q DFT across C-sample chunks
+//                (cols) and a length-C DFT per output residue (rows).
 #include <cuda_runtime.h>
 
 #include "mrdft_fft.cuh"
