@@ -444,9 +444,16 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : (E == kPassElemsLo
   for (int l = threadIdx.x; l < KC * C / 16; l += NT) discard_l2(F + ((int64_t)k0 << CB) + 16 * l);
   const TwQ tw{TQ, CB};
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
-  // w_h^(r k2) = w_h^(k2 (r mod 64)) w_h^(k2 64 (r / 64))
-  auto src = [&](int b, int n) MRDFT_INL -> float2 {
-    return cmul(S[stg<SA, SB>((n << KCB) + b)], cmul(TWL[b * 65 + (n & 63)], TWH[b * (HU + 16 / KC) + (n >> 6)]));
+  // w_h^(r k2) = w_h^(k2 (r mod 64)) w_h^(k2 64 (r / 64)); a first-pass group
+  // reads r = n0 + 2^LRB j with 2^LRB >= 64, so its low factor is shared
+  auto src = [&](int b, int n0, int LRB, auto& v, auto RBc) MRDFT_INL {
+    constexpr int R = 1 << decltype(RBc)::value;
+    const float2 lo = TWL[b * 65 + (n0 & 63)];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int n = n0 + (j << LRB);
+      v[j] = cmul(S[stg<SA, SB>((n << KCB) + b)], cmul(lo, TWH[b * (HU + 16 / KC) + (n >> 6)]));
+    }
   };
   const bool reread = sd.m > i;
   auto store = [&](int b, int k1, float2 ev, float2 odd) MRDFT_INL {
@@ -467,7 +474,8 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : (E == kPassElemsLo
     auto sink = [&](int slot, int b, int k1, float2 odd) MRDFT_INL {
       store(b, k1, cadd(ea[slot], eb[slot]), odd);
     };
-    cg_fft<CB, CB, NT, PTS, true, kPreHalf, KCB>(S, CB, KCB, tw, src, pre, sink);
+    static_assert(3 * ((CB + 2) / 3 - 1) >= 6, "first-pass stride below 64");
+    cg_fft<CB, CB, NT, PTS, true, kPreHalf, KCB, true>(S, CB, KCB, tw, src, pre, sink);
   }
 }
 
