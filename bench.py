@@ -258,6 +258,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cufft", action="store_true")
     ap.add_argument("--no-train", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -307,7 +308,11 @@ def main():
         return replicas.max_over_ranks(v, device=dev)
 
     x_np = make_input(args.workload, rank)
-    plan = _lib.Plan(lengths, len(lengths), real_input=real_input, graph=True)
+    seg_log = streams = None
+    if not args.no_autotune:
+        from paper_1507_02525_gb300 import autotune
+        seg_log, streams = autotune.tune(lengths, len(lengths), real_input)
+    plan = _lib.Plan(lengths, len(lengths), real_input=real_input, graph=True, seg_log=seg_log, streams=streams)
     info = plan.info()
     xt = torch.from_numpy(x_np).to(dev)
     y = torch.empty(plan.out_elems, dtype=torch.complex64, device=dev)
@@ -353,15 +358,7 @@ def main():
     # on the bench stream so that each bracketed kernel has the GPU to itself,
     # on a plan of the same workload without segments (one launch per level
     # over whole signals: the full-size launches the roofline is about)
-    old_seg = os.environ.get("MRDFT_SEG_LOG")
-    os.environ["MRDFT_SEG_LOG"] = "26"
-    try:
-        kplan = _lib.Plan(lengths, len(lengths), real_input=real_input, graph=False)
-    finally:
-        if old_seg is None:
-            del os.environ["MRDFT_SEG_LOG"]
-        else:
-            os.environ["MRDFT_SEG_LOG"] = old_seg
+    kplan = _lib.Plan(lengths, len(lengths), real_input=real_input, graph=False, seg_log=26, streams=1)
     kplan.timing_enable(True, serial=True)
     for _ in range(2):
         kplan.forward(xt.data_ptr(), y.data_ptr(), sp)
@@ -517,6 +514,8 @@ def main():
                        else "working set smaller than L2",
                        "parallelism": f"signals sharded over {world} rank(s), no collective in the path",
                        "graph": True,
+                       "exec_shape": {"seg_log": seg_log, "streams": streams,
+                                      "chosen_by": "autotuner (cached)" if not args.no_autotune else "defaults"},
                        "kernel_source": kernel_source_hash()},
             "hbm_frac_step": round(step_frac, 4),
             "roofline": roof_fwd,

@@ -80,6 +80,19 @@ typedef enum {
 mrdft_status mrdft_plan(mrdft_plan_t* out, const int64_t* lengths, int64_t n_lengths,
                         int64_t batch, int dtype, uint32_t flags);
 
+/*
+ * mrdft_plan_opts -- mrdft_plan with the execution shape chosen explicitly
+ * (no effect on the result, only on speed): signals are cut into segments of
+ * at most 2^seg_log samples whose level chains run concurrently on `streams`
+ * worker streams, so that a segment's levels find their children in L2.
+ * seg_log = 0 or streams = 0 keep the default (2^23, 4 streams; the
+ * environment variables MRDFT_SEG_LOG / MRDFT_STREAMS override a default).
+ * EINVAL unless seg_log is 0 or in [12, 26] and streams in [0, 16].  The
+ * autotuner of the Python package times candidates through this call.
+ */
+mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t n_lengths, int64_t batch,
+                             int dtype, uint32_t flags, int32_t seg_log, int32_t streams);
+
 /* Total complex outputs of the plan, sum_s m_s N_s (the length of y and gy). */
 mrdft_status mrdft_output_elems(mrdft_plan_t plan, int64_t* elems);
 

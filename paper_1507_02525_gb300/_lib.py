@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "MRDFT_OK", 1: "MRDFT_EINVAL", 2: "MRDFT_ENOMEM", 3: "MRDFT_E
                 4: "MRDFT_EUNSUPPORTED", 5: "MRDFT_ETIMEOUT", 6: "MRDFT_EDEVICE"}
 
 # every entry point declared in include/mrdft.h
-EXPORTS = ("mrdft_plan", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
+EXPORTS = ("mrdft_plan", "mrdft_plan_opts", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
            "mrdft_adjoint", "mrdft_forward_host", "mrdft_status_poll", "mrdft_last_error",
            "mrdft_plan_info", "mrdft_timing_enable", "mrdft_timing_read", "mrdft_loss_grad",
            "mrdft_forward_noalloc", "mrdft_destroy")
@@ -64,6 +64,7 @@ def load(build_if_missing: bool = True):
         lib = ctypes.CDLL(LIB_PATH)
         vp, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32
         lib.mrdft_plan.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), i64, i64, i32, u32]
+        lib.mrdft_plan_opts.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), i64, i64, i32, u32, i32, i32]
         lib.mrdft_output_elems.argtypes = [vp, ctypes.POINTER(i64)]
         lib.mrdft_input_elems.argtypes = [vp, ctypes.POINTER(i64)]
         lib.mrdft_forward.argtypes = [vp, vp, vp, vp]
@@ -82,7 +83,7 @@ def load(build_if_missing: bool = True):
         lib.mrdft_forward_noalloc.restype = ctypes.c_int
         lib.mrdft_destroy.argtypes = [vp]
         lib.mrdft_destroy.restype = None
-        for name in ("mrdft_plan", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
+        for name in ("mrdft_plan", "mrdft_plan_opts", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
                      "mrdft_adjoint", "mrdft_forward_host", "mrdft_status_poll", "mrdft_plan_info",
                      "mrdft_timing_enable", "mrdft_timing_read", "mrdft_loss_grad"):
             getattr(lib, name).restype = ctypes.c_int
@@ -107,16 +108,16 @@ class Plan:
     """Owner of an ``mrdft_plan_t`` (see ``mrdft_plan`` in include/mrdft.h)."""
 
     def __init__(self, lengths, batch: int | None = None, real_input: bool = False,
-                 graph: bool = False):
+                 graph: bool = False, seg_log: int | None = None, streams: int | None = None):
         lib = load()
         lengths = [int(v) for v in (lengths if hasattr(lengths, "__len__") else [lengths])]
         if batch is None:
             batch = len(lengths)
         arr = (ctypes.c_int64 * len(lengths))(*lengths)
         h = ctypes.c_void_p()
-        st = lib.mrdft_plan(ctypes.byref(h), arr, len(lengths), int(batch),
-                            MRDFT_R32 if real_input else MRDFT_C64,
-                            MRDFT_FLAG_GRAPH if graph else 0)
+        st = lib.mrdft_plan_opts(ctypes.byref(h), arr, len(lengths), int(batch),
+                                 MRDFT_R32 if real_input else MRDFT_C64,
+                                 MRDFT_FLAG_GRAPH if graph else 0, int(seg_log or 0), int(streams or 0))
         check(st, None)
         self._h = h
         self._lib = lib
@@ -124,6 +125,8 @@ class Plan:
         self.lengths = lengths if len(lengths) == batch else lengths * batch
         self.real_input = real_input
         self.graph = graph
+        self.seg_log = seg_log
+        self.streams = streams
         n = ctypes.c_int64()
         check(lib.mrdft_output_elems(h, ctypes.byref(n)), h)
         self.out_elems = n.value

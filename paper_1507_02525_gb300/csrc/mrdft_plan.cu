@@ -98,8 +98,10 @@ struct mrdft_plan_s {
   LevelItem* d_levels = nullptr;
   std::vector<Segment> segments;
   std::vector<Launch> top;  // levels above seg_log, ascending, whole plan
-  int seg_log = 22;
+  int seg_log = 23;
   int nstreams = 4;
+  bool seg_fixed = false;      // set by mrdft_plan_opts (else the environment may override)
+  bool streams_fixed = false;
   std::vector<cudaStream_t> workers;
   std::vector<cudaEvent_t> ev_join;
   cudaEvent_t ev_fork = nullptr;
@@ -274,10 +276,12 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
 
   // ---- segments: units of <= 2^S samples (whole signals, or windows of 2^S
   // of longer signals), signals ordered by length (longest first)
-  {
+  if (!p->seg_fixed) {
     const char* env = getenv("MRDFT_SEG_LOG");
     if (env) p->seg_log = std::max(kTileLog, std::min(kMaxLog, atoi(env)));
-    env = getenv("MRDFT_STREAMS");
+  }
+  if (!p->streams_fixed) {
+    const char* env = getenv("MRDFT_STREAMS");
     if (env) p->nstreams = std::max(1, std::min(16, atoi(env)));
   }
   const int S = p->seg_log;
@@ -604,7 +608,15 @@ extern "C" {
 
 mrdft_status mrdft_plan(mrdft_plan_t* out, const int64_t* lengths, int64_t n_lengths, int64_t batch,
                         int dtype, uint32_t flags) {
+  return mrdft_plan_opts(out, lengths, n_lengths, batch, dtype, flags, 0, 0);
+}
+
+mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t n_lengths, int64_t batch,
+                             int dtype, uint32_t flags, int32_t seg_log, int32_t streams) {
   if (!out) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: out is NULL");
+  if (seg_log != 0 && (seg_log < kTileLog || seg_log > kMaxLog))
+    return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_opts: seg_log must be 0 or in [12, 26]");
+  if (streams < 0 || streams > 16) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_opts: streams must be in [0, 16]");
   *out = nullptr;
   if (!lengths) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: lengths is NULL");
   if (batch < 1 || batch > (int64_t(1) << 30))
@@ -626,6 +638,14 @@ mrdft_status mrdft_plan(mrdft_plan_t* out, const int64_t* lengths, int64_t n_len
   if (!p) return fail(nullptr, MRDFT_ENOMEM, "mrdft_plan: host allocation failed");
   p->dtype = dtype;
   p->flags = flags;
+  if (seg_log) {
+    p->seg_log = seg_log;
+    p->seg_fixed = true;
+  }
+  if (streams) {
+    p->nstreams = streams;
+    p->streams_fixed = true;
+  }
   mrdft_status st = build_plan(p, lengths, n_lengths, batch);
   if (st != MRDFT_OK) {
     fail(nullptr, st, p->err);

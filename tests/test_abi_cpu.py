@@ -62,11 +62,21 @@ def test_plan_rejects_bad_dtype_and_flags(lib):
     assert _plan(lib, [16], 1, flags=0x80)[0] == 1
 
 
+def test_plan_opts_rejects_bad_shapes(lib):
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int64 * 1)(1 << 16)
+    for seg, streams in ((11, 0), (27, 0), (-1, 0), (0, 17), (0, -2)):
+        st = lib.mrdft_plan_opts(ctypes.byref(h), arr, 1, 1, 0, 0, seg, streams)
+        assert st == 1, (seg, streams)  # MRDFT_EINVAL, before any device work
+        assert h.value is None
+
+
 def test_null_arguments(lib):
     assert lib.mrdft_plan(None, None, 1, 1, 0, 0) == 1
     assert lib.mrdft_forward(None, None, None, None) == 1
     assert lib.mrdft_adjoint(None, None, None, None) == 1
     assert lib.mrdft_forward_host(None, None, None, None) == 1
+    assert lib.mrdft_loss_grad(None, None, None, None, None, None, None) == 1
     assert lib.mrdft_status_poll(None) == 1
     n = ctypes.c_int64()
     assert lib.mrdft_output_elems(None, ctypes.byref(n)) == 1

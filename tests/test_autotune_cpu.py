@@ -1,0 +1,59 @@
+"""Autotuner host logic on CPU: cache keys, the JSON cache and the choice,
+with a fake timer in place of the GPU."""
+import json
+
+import pytest
+
+from paper_1507_02525_gb300 import autotune
+
+
+def test_cache_key_ignores_length_order_and_separates_configs():
+    k1 = autotune.cache_key("GB300", False, 3, [8, 16, 32])
+    k2 = autotune.cache_key("GB300", False, 3, [32, 8, 16])
+    assert k1 == k2
+    assert k1 != autotune.cache_key("GB300", True, 3, [8, 16, 32])
+    assert k1 != autotune.cache_key("GB300", False, 3, [8, 16, 64])
+    assert k1 != autotune.cache_key("other", False, 3, [8, 16, 32])
+
+
+def test_pick_fastest_then_larger_segment():
+    assert autotune.pick({(20, 4): 2.0, (23, 2): 1.5, (22, 4): 1.7}) == (23, 2)
+    assert autotune.pick({(22, 4): 1.0, (23, 4): 1.0}) == (23, 4)
+    with pytest.raises(ValueError):
+        autotune.pick({})
+
+
+def test_tune_times_once_then_reads_cache(tmp_path, monkeypatch):
+    monkeypatch.setenv("MRDFT_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    calls = []
+
+    def timer(s, k):
+        calls.append((s, k))
+        return abs(s - 22) + 0.1 * k
+
+    best = autotune.tune([1 << 24], 1, timer=timer, candidates=[(20, 4), (22, 2), (22, 4), (24, 2)])
+    assert best == (22, 2)
+    assert len(calls) == 4
+    data = json.loads((tmp_path / "tune.json").read_text())
+    (entry,) = data.values()
+    assert entry["seg_log"] == 22 and entry["streams"] == 2 and len(entry["ms"]) == 4
+    calls.clear()
+    assert autotune.tune([1 << 24], 1, timer=timer) == (22, 2)
+    assert calls == []  # served from the cache
+
+
+def test_tune_drops_equivalent_large_segments(tmp_path, monkeypatch):
+    monkeypatch.setenv("MRDFT_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    seen = []
+    autotune.tune([1 << 16] * 4, 4, timer=lambda s, k: seen.append((s, k)) or 1.0,
+                  candidates=[(20, 4), (22, 4), (23, 2), (16, 2)])
+    # signals of 2^16: segments of 2^20, 2^22, 2^23 are all "whole signals"
+    assert (16, 2) in seen and sum(1 for s, _ in seen if s > 16) == 1
+
+
+def test_corrupt_cache_is_ignored(tmp_path, monkeypatch):
+    p = tmp_path / "tune.json"
+    p.write_text("{not json")
+    monkeypatch.setenv("MRDFT_AUTOTUNE_CACHE", str(p))
+    assert autotune.load_cache() == {}
+    assert autotune.tune([256], 1, timer=lambda s, k: float(s), candidates=[(12, 1), (13, 2)]) in [(12, 1), (13, 2)]

@@ -430,3 +430,24 @@ def test_fused_loss_grad_graph_and_repeat():
         torch.cuda.synchronize()
         assert torch.equal(y0, y1) and torch.equal(g0, g1)
         assert abs(float(l1) - float(l0)) <= 1e-9 * abs(float(l0))
+
+
+def test_autotuned_plan(oracle, tmp_path, monkeypatch):
+    """The autotuner picks one of its candidates on the GPU, caches it, and a
+    plan with the tuned shape still matches the oracle."""
+    from paper_1507_02525_gb300 import autotune
+    monkeypatch.setenv("MRDFT_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    cands = [(13, 1), (14, 2), (16, 4)]
+    best = autotune.tune([1 << 16] * 8, 8, candidates=cands, reps=2)
+    assert best in cands
+    assert autotune.tune([1 << 16] * 8, 8, candidates=cands) == best  # cached
+    x = inputs.complex_signals(8, 1 << 16, seed=71)
+    plan = _lib.Plan([1 << 16], 8, seg_log=best[0], streams=best[1])
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty(plan.out_elems, dtype=torch.complex64, device="cuda")
+    plan.forward(xt.data_ptr(), y.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    yn = y.cpu().numpy().reshape(8, 16, 1 << 16)
+    for s in (0, 7):
+        check_forward_levels(yn[s], oracle.forward(x[s].astype(np.complex128)), x[s], f"signal {s}")
+    plan.close()
