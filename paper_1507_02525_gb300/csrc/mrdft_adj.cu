@@ -450,9 +450,11 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
   const TwQ tw{TQ, CB};
   float2* U = a.scratch + sd.aux_off + (w << HB);
   auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[stg<SA, SB>((b << CB) + n)]; };
+  // the intermediate is read by the cols pass right after: keep it in L2
+  const uint64_t keep = l2_evict_last_policy();
   auto sink = [&](int, int b, int r, float2 v) MRDFT_INL {
     const float2 t = cmul(TWL[b * 65 + (r & 63)], TWH[b * (HU + 16 / KC) + (r >> 6)]);
-    __stcg(U + ((int64_t)(k0 + b) << CB) + r, cmulc(conjf2(v), t));
+    st_l2_keep(U + ((int64_t)(k0 + b) << CB) + r, cmulc(conjf2(v), t), keep);
   };
   cg_fft<CB, CB, NT, PTS, false, kPreNone>(S, CB, KCB, tw, src, NoPre{}, sink);
   loss_flush<FUSED>(a, lsum);

@@ -203,6 +203,18 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p) : "memory");
 }
 
+// L2 policy that keeps lines resident ahead of normal and evict-first data,
+// and an 8-byte store that carries it.
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void st_l2_keep(float2* p, float2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;\n" ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol)
+               : "memory");
+}
+
 // Invalidate one 128-byte L2 line without writing it back (dead scratch).
 // p must be 128-byte aligned.
 __device__ __forceinline__ void discard_l2(const void* p) {

@@ -30,6 +30,12 @@ __device__ __forceinline__ float2 load_x1(const FwdArgs& a, int64_t e) {
   if (a.in_real) return make_float2(__ldg(reinterpret_cast<const float*>(a.x) + e), 0.f);
   return __ldg(reinterpret_cast<const float2*>(a.x) + e);
 }
+// the same, marked evict-first in L2 (a level reads its x once; keeping it
+// out of the way lets the level's intermediate stay in L2 until it is used)
+__device__ __forceinline__ float2 load_x1_stream(const FwdArgs& a, int64_t e) {
+  if (a.in_real) return make_float2(__ldcs(reinterpret_cast<const float*>(a.x) + e), 0.f);
+  return __ldcs(reinterpret_cast<const float2*>(a.x) + e);
+}
 // two consecutive samples e, e+1 (e even, 16-byte aligned for complex input)
 __device__ __forceinline__ float4 load_x2(const FwdArgs& a, int64_t e) {
   if (a.in_real) {
@@ -289,8 +295,8 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_fwd_window(const FwdArgs a) 
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int n = threadIdx.x + (t0 + t) * NT;
-      xa[t] = load_x1(a, xs + n);
-      xb[t] = load_x1(a, xs + h + n);
+      xa[t] = load_x1_stream(a, xs + n);
+      xb[t] = load_x1_stream(a, xs + h + n);
     }
     static_for<0, 8>([&](auto TT) MRDFT_INL {
       constexpr int t = decltype(TT)::value;
@@ -372,8 +378,8 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_fwd_cols(cons
     for (int t = 0; t < 8; ++t) {
       const int e = threadIdx.x + (t0 + t) * NT;
       const int64_t n = ((int64_t)(e >> RCB) << CB) + r0 + (e & (RC - 1));
-      xa[t] = load_x1(a, xs + n);
-      xb[t] = load_x1(a, xs + h + n);
+      xa[t] = load_x1_stream(a, xs + n);
+      xb[t] = load_x1_stream(a, xs + h + n);
     }
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
@@ -385,7 +391,9 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_fwd_cols(cons
   __syncthreads();
   float2* F = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
   auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[stg<6, 0>((n << RCB) + b)]; };
-  auto sink = [&](int, int b, int k2, float2 v) MRDFT_INL { __stcg(F + ((int64_t)k2 << CB) + r0 + b, v); };
+  // the intermediate is read by the rows pass right after: keep it in L2
+  const uint64_t keep = l2_evict_last_policy();
+  auto sink = [&](int, int b, int k2, float2 v) MRDFT_INL { st_l2_keep(F + ((int64_t)k2 << CB) + r0 + b, v, keep); };
   cg_fft<QB, QB, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
