@@ -397,6 +397,88 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_fwd_cols(cons
   cg_fft<QB, QB, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
+// Two levels, one read of x: the cols passes of levels i and i + 1 (both with
+// C = 2^11, Q = 2^QB for level i and 2Q for level i + 1).  A CTA takes chunk
+// offsets [r0, r0 + RC) of one level-(i+1) window, whose column strip holds the
+// rows q'' < 4Q; with x_j = x[r + C (q + j Q)] for j = 0..3,
+//   level i + 1 (halves a = rows < 2Q, b = the rest):
+//     z'[q] = (x_0 - x_2) w_{2^(i+1)}^(r + C q),  z'[q + Q] = (x_1 - x_3) w_{2^(i+1)}^(r + C (q + Q))
+//   level i, child c = 0, 1 (its own halves: rows q and q + Q of the child):
+//     z_c[q] = (x_{2c} - x_{2c+1}) w_{2^i}^(r + C q),
+// then DFT_2Q of z' and DFT_Q of z_0, z_1 over q, into the two levels'
+// intermediates.  The rows passes of both levels follow unchanged.
+template <int QB>
+__global__ void __launch_bounds__(kColsThreads, 2) k_fwd_cols2(const FwdArgs a) {
+  constexpr int NT = kColsThreads;
+  constexpr int E = kPassElemsLog;
+  constexpr int CB = 11;
+  constexpr int Q = 1 << QB;
+  constexpr int RCB = E - QB - 2, RC = 1 << RCB;
+  constexpr int UNITS = (Q << RCB) / NT;                 // (q, b) units per thread
+  constexpr int PTS = (1 << (E - 1)) / NT;               // FFT points per thread, each level
+  constexpr int SA1 = QB == 9 ? 6 : 3;                   // staging layouts
+  static_assert(RCB >= 2 && UNITS >= 1, "column blocks of at least 4");
+  extern __shared__ __align__(1024) float2 sm[];
+  float2* Z1 = sm;                                       // level i+1: q' RC + b
+  float2* Z0 = sm + (1 << (E - 1));                      // level i: q 2RC + c RC + b
+  float2* TQ = sm + (1 << E);                            // quarter-wave w_{2^12}
+  float2* ZC1 = TQ + twq_size(12);                       // w_{2^(i+1)}^(r0 + b)
+  float2* ZC0 = ZC1 + RC;                                // w_{2^i}^(r0 + b)
+  const int item = (int)blockIdx.x >> 1;
+  if (item >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
+  const int i1 = a.level, i = i1 - 1;                    // the pair (i, i + 1)
+  const SigDesc sd = a.sigs[it.sig];
+  const int64_t xs = sd.in_off + ((int64_t)it.window << i1);
+  const int r0 = ((it.block << 1) | ((int)blockIdx.x & 1)) << RCB;
+  load_twq<NT>(TQ, 12, a.tw);
+  for (int b = threadIdx.x; b < RC; b += NT) {
+    ZC1[b] = tw_any(a.tw, i1, r0 + b);
+    ZC0[b] = tw_any(a.tw, i, r0 + b);
+  }
+  __syncthreads();
+  const TwQ tw{TQ, 12};
+  float2 xv[UNITS][4];
+#pragma unroll
+  for (int u = 0; u < UNITS; ++u) {
+    const int e = threadIdx.x + u * NT;                  // e = q RC + b
+    const int64_t n = ((int64_t)(e >> RCB) << CB) + r0 + (e & (RC - 1));
+#pragma unroll
+    for (int j = 0; j < 4; ++j) xv[u][j] = load_x1_stream(a, xs + n + ((int64_t)(j * Q) << CB));
+  }
+#pragma unroll
+  for (int u = 0; u < UNITS; ++u) {
+    const int e = threadIdx.x + u * NT;
+    const int q = e >> RCB, b = e & (RC - 1);
+    const float2 w1 = cmul(ZC1[b], twq_l(tw, QB + 2, q));     // w_{2^(i+1)}^(r0 + b + C q)
+    const float2 w0 = cmul(ZC0[b], twq_l(tw, QB + 1, q));     // w_{2^i}^(r0 + b + C q)
+    Z1[stg<SA1, 0>(e)] = cmul(csub(xv[u][0], xv[u][2]), w1);
+    Z1[stg<SA1, 0>(e + (Q << RCB))] = cmul_mj(cmul(csub(xv[u][1], xv[u][3]), w1));  // w_{4Q}^Q = -j
+    const int e0 = (q << (RCB + 1)) + b;
+    Z0[stg<3, 0>(e0)] = cmul(csub(xv[u][0], xv[u][1]), w0);
+    Z0[stg<3, 0>(e0 + RC)] = cmul(csub(xv[u][2], xv[u][3]), w0);
+  }
+  __syncthreads();
+  const uint64_t keep = l2_evict_last_policy();
+  // level i + 1 (window it.window, h = 2^i): intermediate F1[k2][r]
+  float2* F1 = a.scratch2 + sd.aux_off + ((int64_t)it.window << i);
+  auto src1 = [&](int b, int n) MRDFT_INL -> float2 { return Z1[stg<SA1, 0>((n << RCB) + b)]; };
+  auto sink1 = [&](int, int b, int k2, float2 v) MRDFT_INL { st_l2_keep(F1 + ((int64_t)k2 << CB) + r0 + b, v, keep); };
+  cg_fft<QB + 1, QB + 1, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4)>(Z1, QB + 1, RCB, tw, src1, NoPre{}, sink1);
+  // level i (children 2W, 2W + 1, h = 2^(i-1)): sequence s = c RC + b
+  float2* F0 = a.scratch + sd.aux_off + ((int64_t)(2 * it.window) << (i - 1));
+  auto src0 = [&](int s, int n) MRDFT_INL -> float2 { return Z0[stg<3, 0>((n << (RCB + 1)) + s)]; };
+  auto sink0 = [&](int, int s, int k2, float2 v) MRDFT_INL {
+    const int c = s >> RCB, b = s & (RC - 1);
+    st_l2_keep(F0 + ((int64_t)c << (i - 1)) + ((int64_t)k2 << CB) + r0 + b, v, keep);
+  };
+  cg_fft<QB, QB, NT, PTS, true, kPreNone, (RCB + 1 < 4 ? RCB + 1 : 4)>(Z0, QB, RCB + 1, tw, src0, NoPre{}, sink0);
+}
+
+constexpr size_t cols2_smem() {
+  return (size_t)((1 << kPassElemsLog) + twq_size(12) + 2 * (1 << (kPassElemsLog - 5))) * sizeof(float2);
+}
+
 template <int E, int NT, int CB>
 __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : (E == kPassElemsLog ? 2 : 1)) k_fwd_rows(const FwdArgs a) {
   constexpr int PTS = (1 << E) / NT;
@@ -535,6 +617,11 @@ cudaError_t set_fwd_attributes() {
   static_for_host<11, 15>([&](auto C) {
     if (e == cudaSuccess) e = rows_attr<decltype(C)::value>();
   });
+  static_for_host<3, 10>([&](auto Q) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_fwd_cols2<decltype(Q)::value>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)cols2_smem());
+  });
   return e;
 }
 
@@ -557,6 +644,18 @@ cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s) {
   const int QB = (a.level - 1) - cols_log(a.level, false);
   static_for_host<3, 12>([&](auto Q) {
     if (QB == decltype(Q)::value) cols_launch<decltype(Q)::value>(a, grid, s);
+  });
+  return cudaGetLastError();
+}
+bool fwd_cols2_pairable(int upper_level) {
+  const int i = upper_level - 1;
+  return i >= 15 && cols_log(i, false) == 11 && cols_log(upper_level, false) == 11 && i - 12 >= 3 && i - 12 <= 9;
+}
+cudaError_t launch_fwd_cols2(const FwdArgs& a, int grid, cudaStream_t s) {
+  const int QB = (a.level - 2) - 11;
+  static_for_host<3, 10>([&](auto Q) {
+    constexpr int q = decltype(Q)::value;
+    if (QB == q) k_fwd_cols2<q><<<grid << 1, kColsThreads, cols2_smem(), s>>>(a);
   });
   return cudaGetLastError();
 }

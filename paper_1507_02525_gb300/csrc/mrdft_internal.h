@@ -78,6 +78,7 @@ struct FwdArgs {
   int nitems;
   int level;          // large-level kernels: level i being built
   float2* scratch;    // two-pass levels: intermediate, N/2 per signal
+  float2* scratch2;   // dual-level cols: the upper level's intermediate
   Twiddles tw;
   int* status;
 };
@@ -109,6 +110,10 @@ cudaError_t launch_fwd_tile(const FwdArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_fwd_tiny(const FwdArgs& a, int nsig_tiny, cudaStream_t s);
 cudaError_t launch_fwd_window(const FwdArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s);
+// cols passes of levels a.level - 1 and a.level in one read of x; grid =
+// level-a.level items; needs cols_log == 11 and a.level - 12 in [4, 10]
+cudaError_t launch_fwd_cols2(const FwdArgs& a, int grid, cudaStream_t s);
+bool fwd_cols2_pairable(int upper_level);
 cudaError_t launch_fwd_rows(const FwdArgs& a, int grid, cudaStream_t s);
 
 cudaError_t launch_adj_tile(const AdjArgs& a, int grid, cudaStream_t s);

@@ -43,6 +43,16 @@ struct Launch {
   int64_t off;    // first item in d_tiles or d_levels
   int count;      // items (per pass for two-pass levels)
   int64_t bytes;  // algorithmic bytes: input read once + outputs written
+  // two-pass levels i, i + 1 of one chain may share one cols pass (one read of
+  // x for both): dual = 1 on level i, whose cols pass is then k_fwd_cols2 over
+  // the items [c2_off, c2_off + c2_count) of level i + 1, plus the plain cols
+  // pass over [tail_off, tail_off + tail_count), the windows of signals (or
+  // units) that end at level i; dual = 2 on level i + 1 (cols pass done)
+  int dual;
+  int64_t c2_off;
+  int c2_count;
+  int64_t tail_off;  // level-i items of units with U == i (built for every two-pass level)
+  int tail_count;
 };
 
 // A segment: a group of signals or a window of one signal, at most 2^seg_log
@@ -102,13 +112,14 @@ struct mrdft_plan_s {
   int nstreams = 4;
   bool seg_fixed = false;      // set by mrdft_plan_opts (else the environment may override)
   bool streams_fixed = false;
+  bool dual_cols = true;       // pair two-pass levels in one cols pass (MRDFT_DUAL_COLS=0: off)
   std::vector<cudaStream_t> workers;
   std::vector<cudaEvent_t> ev_join;
   cudaEvent_t ev_fork = nullptr;
   float2* d_tw13 = nullptr;
   float2* d_twlo = nullptr;
   float2* d_twhi = nullptr;
-  float2* d_scratch = nullptr;  // N/2 per signal
+  float2* d_scratch = nullptr;  // 2 x N/2 per signal: two-pass intermediates, level parity picks the half
   float2* d_e0 = nullptr;       // N/2 per signal
   float2* d_e1 = nullptr;       // N/2 per signal
   float2* d_acc = nullptr;      // N per signal
@@ -284,6 +295,10 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     const char* env = getenv("MRDFT_STREAMS");
     if (env) p->nstreams = std::max(1, std::min(16, atoi(env)));
   }
+  {
+    const char* env = getenv("MRDFT_DUAL_COLS");
+    if (env) p->dual_cols = atoi(env) != 0;
+  }
   const int S = p->seg_log;
   const int64_t in_b = p->dtype == MRDFT_R32 ? 4 : 8;
   std::vector<int32_t> order(batch);
@@ -324,6 +339,23 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
   std::vector<TileItem> tiles;
   std::vector<LevelItem> litems;
   auto pass_blocks = [](int i) { return pass_items(i); };
+  // consecutive two-pass levels (i, i + 1) of a chain, lowest first: the
+  // upper level's windows, split in halves, are exactly the lower level's
+  // windows of the units that go on to level i + 1 (same item count)
+  auto pair_levels = [&](std::vector<Launch>& chain) {
+    if (!p->dual_cols) return;
+    for (size_t j = 0; j + 1 < chain.size(); ++j) {
+      Launch& L = chain[j];
+      Launch& M = chain[j + 1];
+      if (L.kind != LK_PASS || M.kind != LK_PASS || L.dual || M.level != L.level + 1) continue;
+      if (!fwd_cols2_pairable(M.level) || M.count != L.count - L.tail_count) continue;
+      L.dual = 1;
+      L.c2_off = M.off;
+      L.c2_count = M.count;
+      M.dual = 2;
+      ++j;
+    }
+  };
   auto add_level_items = [&](int i, int32_t sig, int64_t w0, int64_t nw, Launch& L) {
     const int nblk = i <= kWinMaxLog + 1 ? 1 : pass_blocks(i);
     for (int64_t w = w0; w < w0 + nw; ++w)
@@ -374,8 +406,16 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
       for (const Unit& u : units)
         if (u.U >= i) add_level_items(i, u.sig, (int64_t)u.w << (u.U - i), int64_t(1) << (u.U - i), L);
       L.count = (int)((int64_t)litems.size() - L.off);
+      if (L.count && L.kind == LK_PASS) {
+        Launch tail{};
+        L.tail_off = (int64_t)litems.size();
+        for (const Unit& u : units)
+          if (u.U == i) add_level_items(i, u.sig, (int64_t)u.w, 1, tail);
+        L.tail_count = (int)((int64_t)litems.size() - L.tail_off);
+      }
       if (L.count) seg.chain.push_back(L);
     }
+    pair_levels(seg.chain);
     p->segments.push_back(seg);
   }
   // levels above the segments, over whole signals
@@ -387,8 +427,16 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     for (int32_t s : order)
       if (p->sigs[s].m >= i) add_level_items(i, s, 0, int64_t(1) << (p->sigs[s].m - i), L);
     L.count = (int)((int64_t)litems.size() - L.off);
+    if (L.count && L.kind == LK_PASS) {
+      Launch tail{};
+      L.tail_off = (int64_t)litems.size();
+      for (int32_t s : order)
+        if (p->sigs[s].m == i) add_level_items(i, s, 0, 1, tail);
+      L.tail_count = (int)((int64_t)litems.size() - L.tail_off);
+    }
     if (L.count) p->top.push_back(L);
   }
+  pair_levels(p->top);
   p->n_tiles = (int)tiles.size();
   p->n_tiny = (int)tiny_ids.size();
 
@@ -422,7 +470,7 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
   MRDFT_CUDA(p, dev_upload(&p->d_twhi, twhi));
   if (p->max_m > kTileLog) {
     const size_t half = (size_t)p->half_elems * sizeof(float2);
-    cudaError_t e = cudaMalloc(&p->d_scratch, half);
+    cudaError_t e = cudaMalloc(&p->d_scratch, 2 * half);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_e0, half);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_e1, half);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_acc, 2 * half);
@@ -447,8 +495,26 @@ mrdft_status launch_fwd(mrdft_plan_s* p, FwdArgs a, const Launch& L, cudaStream_
     a.items = p->d_levels + L.off;
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_WINDOW, L.bytes, st, [&] { return launch_fwd_window(a, L.count, st); }));
   } else {
+    // the two-pass intermediate of level i lives in half (i & 1) of the scratch
+    a.scratch = p->d_scratch + (L.level & 1) * p->half_elems;
+    if (L.dual == 1) {
+      FwdArgs d = a;
+      d.level = L.level + 1;
+      d.nitems = L.c2_count;
+      d.items = p->d_levels + L.c2_off;
+      d.scratch2 = p->d_scratch + ((L.level + 1) & 1) * p->half_elems;
+      MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_COLS, 0, st, [&] { return launch_fwd_cols2(d, L.c2_count, st); }));
+      if (L.tail_count) {
+        FwdArgs t = a;
+        t.nitems = L.tail_count;
+        t.items = p->d_levels + L.tail_off;
+        MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_COLS, 0, st, [&] { return launch_fwd_cols(t, L.tail_count, st); }));
+      }
+    } else if (L.dual == 0) {
+      a.items = p->d_levels + L.off;
+      MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_COLS, 0, st, [&] { return launch_fwd_cols(a, L.count, st); }));
+    }
     a.items = p->d_levels + L.off;
-    MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_COLS, 0, st, [&] { return launch_fwd_cols(a, L.count, st); }));
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_ROWS, L.bytes, st, [&] { return launch_fwd_rows(a, L.count, st); }));
   }
   return MRDFT_OK;
@@ -744,12 +810,19 @@ const char* mrdft_last_error(mrdft_plan_t p) {
 mrdft_status mrdft_plan_info(mrdft_plan_t p, int32_t* tile_log, int32_t* fwd_launches, int32_t* adj_launches) {
   if (!p) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_info: plan is NULL");
   int n = p->n_tiny ? 1 : 0;
+  int na = n;
+  auto count = [&](const Launch& L) {
+    na += L.kind == LK_PASS ? 2 : 1;
+    if (L.kind != LK_PASS) n += 1;
+    else if (L.dual == 1) n += 2 + (L.tail_count ? 1 : 0);
+    else n += L.dual == 2 ? 1 : 2;
+  };
   for (const Segment& g : p->segments)
-    for (const Launch& L : g.chain) n += L.kind == LK_PASS ? 2 : 1;
-  for (const Launch& L : p->top) n += L.kind == LK_PASS ? 2 : 1;
+    for (const Launch& L : g.chain) count(L);
+  for (const Launch& L : p->top) count(L);
   if (tile_log) *tile_log = kTileLog;
   if (fwd_launches) *fwd_launches = n;
-  if (adj_launches) *adj_launches = n;
+  if (adj_launches) *adj_launches = na;
   return MRDFT_OK;
 }
 

@@ -112,6 +112,31 @@ def test_forward_ragged(oracle, real):
         check_forward_levels(ys_, ref, xs, f"ragged s={s} N={len(xs)}")
 
 
+@pytest.mark.parametrize("seg_log", [15, 16, 23])
+@pytest.mark.parametrize("dual", ["1", "0"])
+def test_forward_dual_cols_ragged(oracle, monkeypatch, seg_log, dual):
+    """Two-pass levels paired in one cols pass (and not): signals that end at
+    the lower level of a pair take the plain cols pass for their windows."""
+    monkeypatch.setenv("MRDFT_DUAL_COLS", dual)
+    lengths = [1 << k for k in (15, 16, 17, 15, 18, 16, 19)]
+    total = sum(lengths)
+    x = inputs.complex_signals(1, total, seed=88)[0]
+    plan = _lib.Plan(lengths, len(lengths), seg_log=seg_log, streams=2)
+    info = plan.info()
+    # a pair with a tail takes cols2 + cols + rows + rows: as many launches as
+    # two unpaired levels; without tails a pair saves one
+    assert info["fwd_launches"] <= info["adj_launches"]
+    uni = _lib.Plan([1 << 18], 2, seg_log=seg_log).info()
+    if dual == "1":
+        assert uni["fwd_launches"] < uni["adj_launches"]
+    else:
+        assert info["fwd_launches"] == info["adj_launches"] and uni["fwd_launches"] == uni["adj_launches"]
+    ys = split_out(run_forward(plan, x), lengths)
+    for s, (xs, ys_) in enumerate(zip(split_in(x, lengths), ys)):
+        ref = oracle.forward(xs.astype(np.complex128))
+        check_forward_levels(ys_, ref, xs, f"dual={dual} S={seg_log} s={s} N={len(xs)}")
+
+
 def test_forward_graph_replay(oracle):
     N, B = 1 << 15, 2
     x = inputs.complex_signals(B, N, seed=5)
