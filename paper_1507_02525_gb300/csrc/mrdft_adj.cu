@@ -527,6 +527,119 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_adj_cols(cons
   cg_fft<QB, QB, NT, PTS, true, kPreHalf, (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, pre, sink);
 }
 
+// Two levels, one update of the accumulated gradient: the cols passes of
+// levels i and i + 1 (both with C = 2^10, Q = 2^QB for level i and 2Q for
+// level i + 1), after both rows passes.  A CTA takes chunk offsets
+// [r0, r0 + RC) of one level-(i+1) window, whose column strip holds the rows
+// q'' < 4Q.  With zb' = IDFT_2Q(U_{i+1}) and zb_c = IDFT_Q(U_i of child c),
+// c1[q''] = conj(w_{2^(i+1)}^(r + C q'')) zb'[q''] and
+// c0_c[q] = conj(w_{2^i}^(r + C q)) zb_c[q], row q + jQ (j = 0..3) of the
+// window receives
+//   j = 0: c1[q] + c0_0[q]        j = 1: c1[q + Q] - c0_0[q]
+//   j = 2: -c1[q] + c0_1[q]       j = 3: -c1[q + Q] - c0_1[q]
+// (the parent's halves a, b and each child's halves), read and written once.
+template <int QB>
+__global__ void __launch_bounds__(kColsThreads, 2) k_adj_cols2(const AdjArgs a) {
+  constexpr int NT = kColsThreads;
+  constexpr int E = kPassElemsLog;
+  constexpr int CB = 10;
+  constexpr int Q = 1 << QB;
+  constexpr int RCB = E - QB - 2, RC = 1 << RCB;
+  constexpr int PTS = (1 << (E - 1)) / NT;               // FFT points per thread, each level
+  constexpr int SA1 = QB == 9 ? 6 : 3;                   // staging layouts
+  static_assert(RCB >= 2 && PTS == 8, "column blocks of at least 4, 8 points per thread");
+  extern __shared__ __align__(1024) float2 sm[];
+  float2* Z1 = sm;                                       // level i+1: k2 RC + b, then c1 at q'' RC + b
+  float2* Z0 = sm + (1 << (E - 1));                      // level i: k2 2RC + c RC + b
+  float2* TQ = sm + (1 << E);                            // quarter-wave w_{2^12}
+  float2* ZC1 = TQ + twq_size(12);                       // w_{2^(i+1)}^(r0 + b)
+  float2* ZC0 = ZC1 + RC;                                // w_{2^i}^(r0 + b)
+  const int item = (int)blockIdx.x >> 1;
+  if (item >= a.nitems) return;
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
+  const int i1 = a.level, i = i1 - 1;                    // the pair (i, i + 1)
+  const SigDesc sd = a.sigs[it.sig];
+  const int64_t W = it.window;
+  const int r0 = ((it.block << 1) | ((int)blockIdx.x & 1)) << RCB;
+  const float2* U1 = a.scratch2 + sd.aux_off + (W << i);
+  const float2* U0 = a.scratch + sd.aux_off + ((2 * W) << (i - 1));
+  float2* acc = a.acc + sd.in_off + (W << i1);
+  const bool add = sd.m > i1;
+  {
+    float2 u1[PTS], u0[PTS];
+#pragma unroll
+    for (int t = 0; t < PTS; ++t) {
+      const int e = threadIdx.x + t * NT;                // e = k2 RC + b, k2 < 2Q
+      u1[t] = __ldcg(U1 + ((int64_t)(e >> RCB) << CB) + r0 + (e & (RC - 1)));
+      const int s = e & (2 * RC - 1), k2 = e >> (RCB + 1);  // e = k2 2RC + s, s = c RC + b
+      u0[t] = __ldcg(U0 + ((int64_t)(s >> RCB) << (i - 1)) + ((int64_t)k2 << CB) + r0 + (s & (RC - 1)));
+    }
+#pragma unroll
+    for (int t = 0; t < PTS; ++t) {
+      const int e = threadIdx.x + t * NT;
+      Z1[stg<SA1, 0>(e)] = conjf2(u1[t]);
+      Z0[stg<3, 0>(e)] = conjf2(u0[t]);
+    }
+  }
+  load_twq<NT>(TQ, 12, a.tw);
+  for (int b = threadIdx.x; b < RC; b += NT) {
+    ZC1[b] = tw_any(a.tw, i1, r0 + b);
+    ZC0[b] = tw_any(a.tw, i, r0 + b);
+  }
+  __syncthreads();
+  // this block's columns of both intermediates are dead: drop them from L2
+  if (RC >= 16) {
+    constexpr int LPR = RC >= 16 ? RC / 16 : 1;          // 128-byte lines per row
+    for (int l = threadIdx.x; l < 4 * Q * LPR; l += NT) {
+      const int row = l / LPR, part = l % LPR;           // rows 0..2Q-1: U1; 2Q..4Q-1: U0 of child (row - 2Q) / Q
+      const float2* p = row < 2 * Q ? U1 + ((int64_t)row << CB)
+                                    : U0 + ((int64_t)((row - 2 * Q) >> QB) << (i - 1)) + ((int64_t)((row - 2 * Q) & (Q - 1)) << CB);
+      discard_l2(p + r0 + 16 * part);
+    }
+  }
+  const TwQ tw{TQ, 12};
+  // level i + 1: zb' per column, c1 back into Z1 in natural order
+  auto src1 = [&](int b, int n) MRDFT_INL -> float2 { return Z1[stg<SA1, 0>((n << RCB) + b)]; };
+  auto sink1 = [&](int, int b, int q, float2 v) MRDFT_INL {
+    Z1[(q << RCB) + b] = cmulc(conjf2(v), cmul(ZC1[b], twq_l(tw, QB + 2, q)));
+  };
+  cg_fft<QB + 1, QB + 1, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4)>(Z1, QB + 1, RCB, tw, src1, NoPre{}, sink1);
+  __syncthreads();
+  // level i: zb_c per (child, column), combined with c1 into the four rows
+  auto src0 = [&](int s, int n) MRDFT_INL -> float2 { return Z0[stg<3, 0>((n << (RCB + 1)) + s)]; };
+  float2 oa[PTS], ob[PTS];
+  auto pre0 = [&](int slot, int s, int q) MRDFT_INL {
+    if (add) {
+      const int64_t n = ((int64_t)(q + ((s >> RCB) << (QB + 1))) << CB) + r0 + (s & (RC - 1));
+      oa[slot] = __ldcg(acc + n);
+      ob[slot] = __ldcg(acc + n + ((int64_t)Q << CB));
+    }
+  };
+  auto sink0 = [&](int slot, int s, int q, float2 v) MRDFT_INL {
+    const int c = s >> RCB, b = s & (RC - 1);
+    const int64_t n = ((int64_t)(q + (c << (QB + 1))) << CB) + r0 + b;
+    const float2 c0 = cmulc(conjf2(v), cmul(ZC0[b], twq_l(tw, QB + 1, q)));
+    float2 ca = Z1[(q << RCB) + b], cb = Z1[((q + Q) << RCB) + b];
+    if (c) {
+      ca = make_float2(-ca.x, -ca.y);
+      cb = make_float2(-cb.x, -cb.y);
+    }
+    ca = cadd(ca, c0);
+    cb = csub(cb, c0);
+    if (add) {
+      ca = cadd(oa[slot], ca);
+      cb = cadd(ob[slot], cb);
+    }
+    __stcg(acc + n, ca);
+    __stcg(acc + n + ((int64_t)Q << CB), cb);
+  };
+  cg_fft<QB, QB, NT, PTS, true, kPreHalf, (RCB + 1 < 4 ? RCB + 1 : 4)>(Z0, QB, RCB + 1, tw, src0, pre0, sink0);
+}
+
+constexpr size_t adj_cols2_smem() {
+  return (size_t)((1 << kPassElemsLog) + twq_size(12) + 2 * (1 << (kPassElemsLog - 6))) * sizeof(float2);
+}
+
 // Launch-time dispatch to the instantiation of a level's FFT sizes.
 template <int QB>
 void adj_cols_launch(const AdjArgs& a, int grid, cudaStream_t s) {
@@ -584,6 +697,11 @@ cudaError_t set_adj_attributes() {
   static_for_host<4, 12>([&](auto Q) {
     if (e == cudaSuccess) e = adj_cols_attr<decltype(Q)::value>();
   });
+  static_for_host<4, 10>([&](auto Q) {
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_adj_cols2<decltype(Q)::value>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)adj_cols2_smem());
+  });
   static_for_host<10, 15>([&](auto C) {
     if (e == cudaSuccess) e = adj_rows_attr<decltype(C)::value>();
   });
@@ -617,6 +735,18 @@ cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s) {
   const int CB = cols_log(a.level, true);
   static_for_host<10, 15>([&](auto C) {
     if (CB == decltype(C)::value) adj_rows_launch<decltype(C)::value>(a, grid, s);
+  });
+  return cudaGetLastError();
+}
+bool adj_cols2_pairable(int upper_level) {
+  const int i = upper_level - 1;
+  return i >= 15 && cols_log(i, true) == 10 && cols_log(upper_level, true) == 10 && i - 11 >= 4 && i - 11 <= 9;
+}
+cudaError_t launch_adj_cols2(const AdjArgs& a, int grid, cudaStream_t s) {
+  const int QB = (a.level - 1) - 11;
+  static_for_host<4, 10>([&](auto Q) {
+    constexpr int q = decltype(Q)::value;
+    if (QB == q) k_adj_cols2<q><<<grid << 1, kColsThreads, adj_cols2_smem(), s>>>(a);
   });
   return cudaGetLastError();
 }

@@ -95,6 +95,7 @@ struct AdjArgs {
   float2* e_out;       // even-bin propagation to level-1 (N/2 per signal)
   float2* acc;         // x_bar contributions of the large levels (N per signal)
   float2* scratch;     // two-pass levels intermediate (N/2 per signal)
+  float2* scratch2;    // dual-level cols: the upper level's intermediate
   int first;           // 1 when this is the top level (no e_in, acc written not added)
   Twiddles tw;
   int* status;
@@ -121,6 +122,11 @@ cudaError_t launch_adj_tiny(const AdjArgs& a, int nsig_tiny, cudaStream_t s);
 cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_adj_cols(const AdjArgs& a, int grid, cudaStream_t s);
+// cols passes of levels a.level - 1 and a.level after both rows passes, one
+// update of acc; grid = level-a.level items; needs cols_log(., adj) == 10 and
+// a.level - 12 in [4, 9]
+cudaError_t launch_adj_cols2(const AdjArgs& a, int grid, cudaStream_t s);
+bool adj_cols2_pairable(int upper_level);
 
 cudaError_t set_kernel_attributes();
 

@@ -591,8 +591,27 @@ mrdft_status launch_adj(mrdft_plan_s* p, AdjArgs a, const Launch& L, cudaStream_
   if (L.kind == LK_WIN) {
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_WINDOW, L.bytes, st, [&] { return launch_adj_window(a, L.count, st); }));
   } else {
+    // the two-pass intermediate of level i lives in half (i & 1) of the scratch;
+    // a paired upper level leaves its cols pass to the lower level's launch,
+    // which runs it with its own after both rows passes
+    a.scratch = p->d_scratch + (L.level & 1) * p->half_elems;
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_ROWS, L.bytes, st, [&] { return launch_adj_rows(a, L.count, st); }));
-    MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_COLS, 0, st, [&] { return launch_adj_cols(a, L.count, st); }));
+    if (L.dual == 1 && adj_cols2_pairable(L.level + 1)) {
+      AdjArgs d = a;
+      d.level = L.level + 1;
+      d.nitems = L.c2_count;
+      d.items = p->d_levels + L.c2_off;
+      d.scratch2 = p->d_scratch + ((L.level + 1) & 1) * p->half_elems;
+      MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_COLS, 0, st, [&] { return launch_adj_cols2(d, L.c2_count, st); }));
+      if (L.tail_count) {
+        AdjArgs t = a;
+        t.nitems = L.tail_count;
+        t.items = p->d_levels + L.tail_off;
+        MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_COLS, 0, st, [&] { return launch_adj_cols(t, L.tail_count, st); }));
+      }
+    } else if (!(L.dual == 2 && adj_cols2_pairable(L.level))) {
+      MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_COLS, 0, st, [&] { return launch_adj_cols(a, L.count, st); }));
+    }
   }
   return MRDFT_OK;
 }
@@ -812,7 +831,9 @@ mrdft_status mrdft_plan_info(mrdft_plan_t p, int32_t* tile_log, int32_t* fwd_lau
   int n = p->n_tiny ? 1 : 0;
   int na = n;
   auto count = [&](const Launch& L) {
-    na += L.kind == LK_PASS ? 2 : 1;
+    if (L.kind != LK_PASS) na += 1;
+    else if (L.dual == 1 && adj_cols2_pairable(L.level + 1)) na += 2 + (L.tail_count ? 1 : 0);
+    else na += L.dual == 2 && adj_cols2_pairable(L.level) ? 1 : 2;
     if (L.kind != LK_PASS) n += 1;
     else if (L.dual == 1) n += 2 + (L.tail_count ? 1 : 0);
     else n += L.dual == 2 ? 1 : 2;

@@ -122,15 +122,16 @@ def test_forward_dual_cols_ragged(oracle, monkeypatch, seg_log, dual):
     total = sum(lengths)
     x = inputs.complex_signals(1, total, seed=88)[0]
     plan = _lib.Plan(lengths, len(lengths), seg_log=seg_log, streams=2)
-    info = plan.info()
-    # a pair with a tail takes cols2 + cols + rows + rows: as many launches as
-    # two unpaired levels; without tails a pair saves one
-    assert info["fwd_launches"] <= info["adj_launches"]
+    # without tails a pair of levels saves one launch in each direction (a pair
+    # with a tail takes cols2 + cols + rows + rows, as many as two levels)
     uni = _lib.Plan([1 << 18], 2, seg_log=seg_log).info()
+    monkeypatch.setenv("MRDFT_DUAL_COLS", "0")
+    base = _lib.Plan([1 << 18], 2, seg_log=seg_log).info()
+    monkeypatch.setenv("MRDFT_DUAL_COLS", dual)
     if dual == "1":
-        assert uni["fwd_launches"] < uni["adj_launches"]
+        assert uni["fwd_launches"] < base["fwd_launches"] and uni["adj_launches"] < base["adj_launches"]
     else:
-        assert info["fwd_launches"] == info["adj_launches"] and uni["fwd_launches"] == uni["adj_launches"]
+        assert uni == base
     ys = split_out(run_forward(plan, x), lengths)
     for s, (xs, ys_) in enumerate(zip(split_in(x, lengths), ys)):
         ref = oracle.forward(xs.astype(np.complex128))
@@ -306,6 +307,22 @@ def test_adjoint_ragged(oracle):
     for s in range(len(lengths)):
         ref = oracle.adjoint(gys[s].astype(np.complex128))
         check_adjoint(gx[s], ref, gys[s], f"ragged s={s}")
+
+
+@pytest.mark.parametrize("seg_log", [15, 16, 23])
+@pytest.mark.parametrize("dual", ["1", "0"])
+def test_adjoint_dual_cols_ragged(oracle, monkeypatch, seg_log, dual):
+    """Adjoint with two-pass levels paired in one cols pass (and not),
+    including signals that end at the lower level of a pair."""
+    monkeypatch.setenv("MRDFT_DUAL_COLS", dual)
+    lengths = [1 << k for k in (15, 16, 17, 15, 18, 16, 19, 20)]
+    plan = _lib.Plan(lengths, len(lengths), seg_log=seg_log, streams=2)
+    gy = inputs.complex_signals(1, plan.out_elems, seed=90)[0]
+    gx = split_in(run_adjoint(plan, gy), lengths)
+    gys = split_out(gy, lengths)
+    for s in range(len(lengths)):
+        ref = oracle.adjoint(gys[s].astype(np.complex128))
+        check_adjoint(gx[s], ref, gys[s], f"dual={dual} S={seg_log} s={s}")
 
 
 def test_adjoint_dot_product():
