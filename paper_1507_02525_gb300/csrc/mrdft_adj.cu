@@ -152,14 +152,6 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
   const SigDesc sd0 = a.sigs[a.sig_ids[it.sig_list]];
   const bool below = sd0.m > tl;
   __syncthreads();
-  // every level reads its gradient slice once, in a latency-bound burst: keep
-  // the next two levels' slices on their way into L2 (one bulk request per signal)
-  auto prefetch_level = [&](int lv) MRDFT_INL {
-    if (lv >= 1 && tid < it.nsig)
-      prefetch_l2_bulk(a.gy + TS[tid].g_base + ((int64_t)(lv - 1) << TS[tid].m), (uint32_t)(sizeof(float2) << tl));
-  };
-  prefetch_level(tl);
-  prefetch_level(tl - 1);
 #pragma unroll 4
   for (int c = tid; c < (Tn >> 1); c += NT) {
     const int e = c << 1;
@@ -194,11 +186,6 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     if (i > tl) return;
     constexpr int L = 1 << i, h = L >> 1;
     constexpr int SA = i <= 10 ? 3 : 6;  // staging layout of the odd half
-    prefetch_level(i - 2);
-    if constexpr (i == 5) {  // levels 2 and 1 follow level 3 in registers
-      prefetch_level(2);
-      prefetch_level(1);
-    }
     const float2* Ein = E[(i + 1) & 1];
     float2* Eout = E[i & 1];
     // G_i = g_i + P_i: even half -> Eout, conj(odd half) -> Z
@@ -319,9 +306,6 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) 
   const int64_t w = it.window;
   const bool add = sd.m > i;
   float2* acc = a.acc + sd.in_off + (w << i);
-  // the accumulator is read only after the FFT: start moving it into L2 now
-  if (add && threadIdx.x < 2 * (h / 2048))
-    prefetch_l2_bulk(acc + (threadIdx.x >> 1) * 2048 + (threadIdx.x & 1) * h, 2048 * sizeof(float2));
   load_twq<NT>(TQ, 13, a.tw);
   const float2 w1 = __ldg(&a.tw.tw13[1]);  // w_{2^14}
   float lsum = 0.f;  // fused loss: this thread's share

@@ -193,16 +193,6 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// Start moving [p, p + bytes) into L2 (bulk, no registers, no completion
-// wait); p and bytes multiples of 16.
-__device__ __forceinline__ void prefetch_l2_bulk(const void* p, uint32_t bytes) {
-  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
-}
-// Start moving the L2 line holding p into L2.
-__device__ __forceinline__ void prefetch_l2(const void* p) {
-  asm volatile("prefetch.global.L2 [%0];\n" ::"l"(p) : "memory");
-}
-
 // L2 policy that keeps lines resident ahead of normal and evict-first data,
 // and an 8-byte store that carries it.
 __device__ __forceinline__ uint64_t l2_evict_last_policy() {

@@ -138,21 +138,6 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
     TS[tid] = TileSig{sd.in_off + t0, sd.out_off + t0, sd.m, 0};
   }
   __syncthreads();
-  // a tile that will run about one wave later (2 CTAs on each of ~152 SMs):
-  // start moving its x into L2 now, so that its staging is served from L2
-  if (tid == 0) {
-    const int fut = item + 2 * 152;
-    if (fut < a.nitems) {
-      const TileItem fi = reinterpret_cast<const TileItem*>(a.items)[fut];
-      if (fi.nsig == 1) {
-        const SigDesc fs = a.sigs[a.sig_ids[fi.sig_list]];
-        const int es = a.in_real ? 4 : 8;
-        const char* p = reinterpret_cast<const char*>(a.x) + (fs.in_off + ((int64_t)fi.tile << fi.tlog)) * es;
-        if ((reinterpret_cast<uintptr_t>(p) & 15) == 0) prefetch_l2_bulk(p, (uint32_t)(es << fi.tlog));
-      }
-    }
-  }
-
   // ---- stage the tile of x (P^(1): x is read once and reused per level)
   if (!a.in_real) {
     const float2* xg = reinterpret_cast<const float2*>(a.x);
@@ -270,9 +255,6 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_fwd_window(const FwdArgs a) 
   const int64_t xs = sd.in_off + ws;
   const float2* yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
   float2* ycur = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ws;
-  // the children are read only after the FFT: start moving them into L2 now
-  if (threadIdx.x < 2 * (h / 2048))
-    prefetch_l2_bulk(yprev + (threadIdx.x >> 1) * 2048 + (threadIdx.x & 1) * h, 2048 * sizeof(float2));
   load_twq<NT>(TQ, 13, a.tw);
   // w_{2^14}^n = w_{2^13}^(n/2) w_{2^14}^(n mod 2)
   const float2 w1 = __ldg(&a.tw.tw13[1]);
@@ -361,10 +343,6 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_fwd_cols(cons
   const int64_t xs = sd.in_off + ((int64_t)it.window << i);
   const int r0 = ((it.block << SH) | ((int)blockIdx.x & ((1 << SH) - 1))) << RCB;
   const int64_t h = (int64_t)1 << HB;
-  // x rows r0 .. r0 + RC of every chunk q, both halves: start moving them into
-  // L2 (the loads below come in batches)
-  for (int q = threadIdx.x; q < 2 << QB; q += NT) prefetch_l2(reinterpret_cast<const char*>(a.x) +
-      (xs + (int64_t)(q >> 1) * (1 << CB) + (q & 1) * h + r0) * (a.in_real ? 4 : 8));
   load_twq<NT>(TQ, 12, a.tw);
   for (int r = threadIdx.x; r < RC; r += NT) ZC[r] = tw_any(a.tw, i, r0 + r);
   __syncthreads();
