@@ -483,7 +483,7 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_adj_cols(cons
   for (int r = threadIdx.x; r < RC; r += NT) ZC[r] = tw_any(a.tw, i, r0 + r);
   __syncthreads();
   // this block's columns of the intermediate are dead: drop them from L2
-  if (RC >= 16)
+  if constexpr (RC >= 16)
     for (int l = threadIdx.x; l < (RC / 16) << QB; l += NT)
       discard_l2(U + ((int64_t)(l >> (RCB - 4)) << CB) + r0 + 16 * (l & ((RC / 16) - 1)));
   const TwQ tw{TQ, 12};

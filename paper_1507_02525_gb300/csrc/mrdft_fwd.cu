@@ -309,10 +309,9 @@ constexpr size_t cols_smem(int E) { return (size_t)((1 << E) + twq_size(12) + (1
 // cols CTAs of 2^12 points (4 per SM) where Q <= 2^10 keeps chunks of >= 4
 template <int QB>
 constexpr int cols_e() { return QB <= 10 ? 12 : kPassElemsLog; }
-// rows pass: work area, w_C table, twiddle tables KC (64 + 1) + KC (C / 64 + 1)
-// <= 4 * 65 + 2^(E-6) + 4
+// rows pass: work area, w_C table, twiddle tables KC (64 + 1) + KC (C / 64 + 16 / KC)
 constexpr size_t rows_smem(int E, int CB) {
-  return (size_t)((1 << E) + twq_size(CB) + 4 * 65 + (1 << (E - 6)) + 16) * sizeof(float2);
+  return (size_t)((1 << E) + twq_size(CB) + (1 << (E - CB)) * 65 + (1 << (E - 6)) + 16) * sizeof(float2);
 }
 
 // =============================================================== two-pass
@@ -385,11 +384,10 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_fwd_cols(cons
 //     z_c[q] = (x_{2c} - x_{2c+1}) w_{2^i}^(r + C q),
 // then DFT_2Q of z' and DFT_Q of z_0, z_1 over q, into the two levels'
 // intermediates.  The rows passes of both levels follow unchanged.
-template <int QB>
+template <int QB, int CB>
 __global__ void __launch_bounds__(kColsThreads, 2) k_fwd_cols2(const FwdArgs a) {
   constexpr int NT = kColsThreads;
   constexpr int E = kPassElemsLog;
-  constexpr int CB = 11;
   constexpr int Q = 1 << QB;
   constexpr int RCB = E - QB - 2, RC = 1 << RCB;
   constexpr int UNITS = (Q << RCB) / NT;                 // (q, b) units per thread
@@ -469,7 +467,7 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : (E == kPassElemsLo
   float2* S = sm;                          // sequence j position r at r KC + j (staging, then zlay)
   float2* TQ = sm + (1 << E);              // quarter-wave w_C
   float2* TWL = TQ + twq_size(CB);         // [KC][64] (row stride 65): w_h^(k2 t)
-  float2* TWH = TWL + 4 * 65;              // [KC][C/64] (row stride C/64 + 16/KC): w_h^(k2 64 u)
+  float2* TWH = TWL + KC * 65;             // [KC][C/64] (row stride C/64 + 16/KC): w_h^(k2 64 u)
   int item, blk;
   if constexpr (SH >= 0) {
     item = (int)blockIdx.x << SH;
@@ -560,7 +558,8 @@ template <int CB>
 void rows_launch(const FwdArgs& a, int grid, cudaStream_t s) {
   constexpr int E = rows_e<CB>();
   constexpr int NT = E < kPassElemsLog ? kPassThreads : (E == kPassElemsLog ? kColsThreads : kPassThreadsWide);
-  k_fwd_rows<E, NT, CB><<<rows_grid(a.level, false, grid), NT, rows_smem(E, CB), s>>>(a);
+  // a CTA of 2^E points takes 2^(E-13) items (E >= 13)
+  k_fwd_rows<E, NT, CB><<<grid >> (E - kPassElemsLog), NT, rows_smem(E, CB), s>>>(a);
 }
 template <int QB>
 cudaError_t cols_attr() {
@@ -592,13 +591,15 @@ cudaError_t set_fwd_attributes() {
   static_for_host<3, 12>([&](auto Q) {
     if (e == cudaSuccess) e = cols_attr<decltype(Q)::value>();
   });
-  static_for_host<11, 15>([&](auto C) {
+  static_for_host<10, 15>([&](auto C) {
     if (e == cudaSuccess) e = rows_attr<decltype(C)::value>();
   });
-  static_for_host<3, 10>([&](auto Q) {
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_fwd_cols2<decltype(Q)::value>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)cols2_smem());
+  static_for_host<10, 12>([&](auto C) {
+    static_for_host<3, 10>([&](auto Q) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_fwd_cols2<decltype(Q)::value, decltype(C)::value>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cols2_smem());
+    });
   });
   return e;
 }
@@ -618,28 +619,35 @@ cudaError_t launch_fwd_window(const FwdArgs& a, int grid, cudaStream_t s) {
     k_fwd_window<13><<<grid, kWinThreads, kWinSmem, s>>>(a);
   return cudaGetLastError();
 }
+// C = 2^fwd_cb of a two-pass level (Q = h / C <= 2^11 keeps cols chunks of >= 4)
+static int fwd_cb(int cb_min, int i) {
+  const int m = cb_min ? cb_min : 10;
+  return (i - 1) - 11 > m ? (i - 1) - 11 : m;
+}
 cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s) {
-  const int QB = (a.level - 1) - cols_log(a.level, false);
+  const int QB = (a.level - 1) - fwd_cb(a.cb_min, a.level);
   static_for_host<3, 12>([&](auto Q) {
     if (QB == decltype(Q)::value) cols_launch<decltype(Q)::value>(a, grid, s);
   });
   return cudaGetLastError();
 }
-bool fwd_cols2_pairable(int upper_level) {
-  const int i = upper_level - 1;
-  return i >= 15 && cols_log(i, false) == 11 && cols_log(upper_level, false) == 11 && i - 12 >= 3 && i - 12 <= 9;
+bool fwd_cols2_pairable(int upper_level, int cb_min) {
+  const int i = upper_level - 1, CB = fwd_cb(cb_min, i), QB = (i - 1) - CB;
+  return i >= 15 && fwd_cb(cb_min, upper_level) == CB && (CB == 10 || CB == 11) && QB >= 3 && QB <= 9;
 }
 cudaError_t launch_fwd_cols2(const FwdArgs& a, int grid, cudaStream_t s) {
-  const int QB = (a.level - 2) - 11;
-  static_for_host<3, 10>([&](auto Q) {
-    constexpr int q = decltype(Q)::value;
-    if (QB == q) k_fwd_cols2<q><<<grid << 1, kColsThreads, cols2_smem(), s>>>(a);
+  const int i = a.level - 1, CB = fwd_cb(a.cb_min, i), QB = (i - 1) - CB;
+  static_for_host<10, 12>([&](auto C) {
+    static_for_host<3, 10>([&](auto Q) {
+      constexpr int q = decltype(Q)::value, c = decltype(C)::value;
+      if (QB == q && CB == c) k_fwd_cols2<q, c><<<grid << 1, kColsThreads, cols2_smem(), s>>>(a);
+    });
   });
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_rows(const FwdArgs& a, int grid, cudaStream_t s) {
-  const int CB = cols_log(a.level, false);
-  static_for_host<11, 15>([&](auto C) {
+  const int CB = fwd_cb(a.cb_min, a.level);
+  static_for_host<10, 15>([&](auto C) {
     if (CB == decltype(C)::value) rows_launch<decltype(C)::value>(a, grid, s);
   });
   return cudaGetLastError();

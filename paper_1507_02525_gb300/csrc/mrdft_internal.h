@@ -43,18 +43,16 @@ constexpr int kTileThreads = 256;            // 16 samples per thread, 2 CTAs pe
 constexpr int kWinMaxLog = 13;               // one CTA FFT holds up to 2^13 points
 constexpr int kWinThreads = 256;             // levels 13, 14: 16 or 32 points per thread
 // Two-pass levels (i >= 15), h = 2^(i-1) = Q * C with C = 2^cols_log(i):
-//   forward: 2^11 up to level 23, then 2^(i-12); adjoint: 2^10 up to level
-//   22, then 2^(i-12) -- so that Q <= 2^11 and every cols CTA reads chunks of
-//   at least 4 consecutive samples.
+//   2^10 up to level 22, then 2^(i-12), so that Q <= 2^11 and every cols CTA
+//   reads chunks of at least 4 consecutive samples (the forward can take
+//   C = 2^11 up to level 23 instead: FwdArgs.cb_min).
 //   cols pass: 2^13 points per CTA (RC = 2^13 / Q chunk offsets), 2 CTAs/SM
 //   rows pass: 2^rows_elems_log(i) points per CTA (KC = 2^E / C residues).
 constexpr int kPassElemsLog = 13;
 constexpr int kPassThreads = 256;        // 2^13-point rows / adjoint cols CTAs
 constexpr int kColsThreads = 512;        // forward cols and 2^12-point adjoint rows CTAs (64 registers)
 constexpr int kPassThreadsWide = 512;    // the 2^14-point rows CTA (level 26)
-__host__ __device__ constexpr int cols_log(int i, bool adj) {
-  return (i - 1) - 11 > (adj ? 10 : 11) ? (i - 1) - 11 : (adj ? 10 : 11);
-}
+__host__ __device__ constexpr int cols_log(int i, bool) { return (i - 1) - 11 > 10 ? (i - 1) - 11 : 10; }
 // rows CTA size: 2^12 points for the adjoint's C = 2^10, else 2^13 (2^14 for C = 2^14)
 __host__ __device__ constexpr int rows_elems_log_c(int cb, bool adj) {
   return (adj && cb <= 10) ? 12 : (cb > 13 ? cb : 13);
@@ -79,6 +77,7 @@ struct FwdArgs {
   int level;          // large-level kernels: level i being built
   float2* scratch;    // two-pass levels: intermediate, N/2 per signal
   float2* scratch2;   // dual-level cols: the upper level's intermediate
+  int cb_min;         // two-pass levels: C = 2^max(i - 12, cb_min), cb_min 10 or 11 (0 means 10)
   Twiddles tw;
   int* status;
 };
@@ -112,9 +111,9 @@ cudaError_t launch_fwd_tiny(const FwdArgs& a, int nsig_tiny, cudaStream_t s);
 cudaError_t launch_fwd_window(const FwdArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s);
 // cols passes of levels a.level - 1 and a.level in one read of x; grid =
-// level-a.level items; needs cols_log == 11 and a.level - 12 in [4, 10]
+// level-a.level items; both levels with the same C, Q of the lower in [2^3, 2^9]
 cudaError_t launch_fwd_cols2(const FwdArgs& a, int grid, cudaStream_t s);
-bool fwd_cols2_pairable(int upper_level);
+bool fwd_cols2_pairable(int upper_level, int cb_min);
 cudaError_t launch_fwd_rows(const FwdArgs& a, int grid, cudaStream_t s);
 
 cudaError_t launch_adj_tile(const AdjArgs& a, int grid, cudaStream_t s);

@@ -113,6 +113,7 @@ struct mrdft_plan_s {
   bool seg_fixed = false;      // set by mrdft_plan_opts (else the environment may override)
   bool streams_fixed = false;
   bool dual_cols = true;       // pair two-pass levels in one cols pass (MRDFT_DUAL_COLS=0: off)
+  int fwd_cb_min = 10;         // forward two-pass levels: C = 2^max(i - 12, fwd_cb_min) (MRDFT_FWD_CB=11)
   std::vector<cudaStream_t> workers;
   std::vector<cudaEvent_t> ev_join;
   cudaEvent_t ev_fork = nullptr;
@@ -122,6 +123,11 @@ struct mrdft_plan_s {
   float2* d_scratch = nullptr;  // 2 x N/2 per signal: two-pass intermediates, level parity picks the half
   float2* d_e0 = nullptr;       // N/2 per signal
   float2* d_e1 = nullptr;       // N/2 per signal
+  // the lowest top level's even-bin propagation (N/2 per signal), read by
+  // the level-seg_log launches of every segment: the two segments of one
+  // parent window run on different worker streams, and each writes its own
+  // lower levels' propagation into d_e0 / d_e1 over the parent's range
+  float2* d_etop = nullptr;
   float2* d_acc = nullptr;      // N per signal
   int* d_status = nullptr;
   void* d_stage_x = nullptr;
@@ -241,7 +247,7 @@ void release(mrdft_plan_s* p) {
   p->adj_graphs.clear();
   void* ptrs[] = {p->d_sigs, p->d_tile_ids, p->d_tiles, p->d_tiny_ids, p->d_levels,
                   p->d_tw13, p->d_twlo, p->d_twhi, p->d_scratch, p->d_e0,
-                  p->d_e1, p->d_acc, p->d_status, p->d_stage_x, p->d_stage_y};
+                  p->d_e1, p->d_etop, p->d_acc, p->d_status, p->d_stage_x, p->d_stage_y};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -298,6 +304,8 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
   {
     const char* env = getenv("MRDFT_DUAL_COLS");
     if (env) p->dual_cols = atoi(env) != 0;
+    env = getenv("MRDFT_FWD_CB");
+    if (env) p->fwd_cb_min = atoi(env) == 11 ? 11 : 10;
   }
   const int S = p->seg_log;
   const int64_t in_b = p->dtype == MRDFT_R32 ? 4 : 8;
@@ -348,7 +356,7 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
       Launch& L = chain[j];
       Launch& M = chain[j + 1];
       if (L.kind != LK_PASS || M.kind != LK_PASS || L.dual || M.level != L.level + 1) continue;
-      if (!fwd_cols2_pairable(M.level) || M.count != L.count - L.tail_count) continue;
+      if (!fwd_cols2_pairable(M.level, p->fwd_cb_min) || M.count != L.count - L.tail_count) continue;
       L.dual = 1;
       L.c2_off = M.off;
       L.c2_count = M.count;
@@ -473,6 +481,7 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     cudaError_t e = cudaMalloc(&p->d_scratch, 2 * half);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_e0, half);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_e1, half);
+    if (e == cudaSuccess && !p->top.empty()) e = cudaMalloc(&p->d_etop, half);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_acc, 2 * half);
     if (e != cudaSuccess) return fail(p, MRDFT_ENOMEM, std::string("scratch allocation: ") + cudaGetErrorString(e));
   }
@@ -552,6 +561,7 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
   a.y = reinterpret_cast<float2*>(y);
   a.sigs = p->d_sigs;
   a.scratch = p->d_scratch;
+  a.cb_min = p->fwd_cb_min;
   a.tw = twiddles(p);
   a.status = p->d_status;
   if (p->n_tiny) {
@@ -575,19 +585,24 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
   return MRDFT_OK;
 }
 
-mrdft_status launch_adj(mrdft_plan_s* p, AdjArgs a, const Launch& L, cudaStream_t st) {
+// Even-bin propagation buffers: level i writes d_e[i & 1] and reads
+// d_e[(i + 1) & 1], except across the boundary between the top chain and the
+// segments, which goes through d_etop.
+mrdft_status launch_adj(mrdft_plan_s* p, AdjArgs a, const Launch& L, cudaStream_t st, bool in_top) {
+  const int S = p->seg_log;
+  auto ebuf = [&](int lv) { return (lv & 1) ? p->d_e1 : p->d_e0; };
   a.level = L.level;
   a.nitems = L.count;
   if (L.kind == LK_TILE) {
     a.sig_ids = p->d_tile_ids;
     a.items = p->d_tiles + L.off;
-    a.e_in = ((kTileLog + 1) & 1) ? p->d_e1 : p->d_e0;
+    a.e_in = (!in_top && S == kTileLog && p->d_etop) ? p->d_etop : ebuf(kTileLog + 1);
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_TILE, L.bytes, st, [&] { return launch_adj_tile(a, L.count, st); }));
     return MRDFT_OK;
   }
   a.items = p->d_levels + L.off;
-  a.e_out = (L.level & 1) ? p->d_e1 : p->d_e0;
-  a.e_in = ((L.level + 1) & 1) ? p->d_e1 : p->d_e0;
+  a.e_out = (in_top && L.level == S + 1) ? p->d_etop : ebuf(L.level);
+  a.e_in = (!in_top && L.level == S && p->d_etop) ? p->d_etop : ebuf(L.level + 1);
   if (L.kind == LK_WIN) {
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_WINDOW, L.bytes, st, [&] { return launch_adj_window(a, L.count, st); }));
   } else {
@@ -628,12 +643,12 @@ mrdft_status enqueue_adjoint(mrdft_plan_s* p, const void* gy, void* gx, cudaStre
   a.t = p->cur_t;
   a.loss = p->cur_loss;
   for (auto it = p->top.rbegin(); it != p->top.rend(); ++it) {
-    mrdft_status r = launch_adj(p, a, *it, st);
+    mrdft_status r = launch_adj(p, a, *it, st, true);
     if (r != MRDFT_OK) return r;
   }
   mrdft_status r = run_segments(p, st, [&](const Segment& seg, cudaStream_t s) {
     for (auto it = seg.chain.rbegin(); it != seg.chain.rend(); ++it) {
-      mrdft_status q = launch_adj(p, a, *it, s);
+      mrdft_status q = launch_adj(p, a, *it, s, false);
       if (q != MRDFT_OK) return q;
     }
     return MRDFT_OK;

@@ -138,6 +138,23 @@ def test_forward_dual_cols_ragged(oracle, monkeypatch, seg_log, dual):
         check_forward_levels(ys_, ref, xs, f"dual={dual} S={seg_log} s={s} N={len(xs)}")
 
 
+@pytest.mark.parametrize("cb", ["10", "11"])
+@pytest.mark.parametrize("m", [15, 16, 19, 22])
+def test_forward_two_pass_split(oracle, monkeypatch, cb, m):
+    """Both splits of the two-pass levels, h = Q C with C = 2^max(i - 12, cb)."""
+    monkeypatch.setenv("MRDFT_FWD_CB", cb)
+    N = 1 << m
+    x = inputs.complex_signals(1, N, seed=300 + m)[0]
+    y = run_forward(_lib.Plan([N], 1), x).reshape(m, N)
+    x128 = x.astype(np.complex128)
+    xn = float(np.linalg.norm(x128))
+    for i in range(13, m + 1):
+        ref = oracle.forward_level(x128, i)
+        d = y[i - 1].astype(np.complex128) - ref
+        assert np.linalg.norm(d) / np.linalg.norm(ref) <= REL_PER_LEVEL * i, f"C=2^{cb} level {i}"
+        assert np.abs(d).max() <= ABS_FRAC * xn, f"C=2^{cb} level {i} max abs"
+
+
 def test_forward_graph_replay(oracle):
     N, B = 1 << 15, 2
     x = inputs.complex_signals(B, N, seed=5)
@@ -336,6 +353,46 @@ def test_adjoint_dot_product():
     lhs = np.vdot(g.reshape(-1).astype(np.complex128), y)
     rhs = np.vdot(gx, x.reshape(-1).astype(np.complex128))
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+@pytest.mark.parametrize("seg_log", [12, 13, 14, 16])
+def test_adjoint_long_signal_segments(oracle, seg_log):
+    """Signals longer than a segment: the segments of one parent window run
+    concurrently on worker streams and read the top level's propagation while
+    transforming their own levels (repeated to give a race a chance)."""
+    lengths = [1 << 18, 1 << 16, 1 << 17]
+    plan = _lib.Plan(lengths, len(lengths), seg_log=seg_log, streams=4)
+    gy = inputs.complex_signals(1, plan.out_elems, seed=91)[0]
+    gys = split_out(gy, lengths)
+    refs = [oracle.adjoint(g.astype(np.complex128)) for g in gys]
+    for rep in range(3):
+        gx = split_in(run_adjoint(plan, gy), lengths)
+        for s in range(len(lengths)):
+            check_adjoint(gx[s], refs[s], gys[s], f"S={seg_log} rep={rep} s={s}")
+
+
+def test_adjoint_dot_product_16m():
+    """<M x, g> = <x, M^H g> at N = 2^24 with the default execution shape
+    (two segments of 2^23 under one top level), sums in FP64 on the GPU."""
+    N = 1 << 24
+    plan = _lib.Plan([N], 1)
+    gen = torch.Generator(device="cuda").manual_seed(24)
+    x = torch.randn(N, dtype=torch.complex64, device="cuda", generator=gen)
+    g = torch.randn(plan.out_elems, dtype=torch.complex64, device="cuda", generator=gen)
+    y = torch.empty(plan.out_elems, dtype=torch.complex64, device="cuda")
+    gx = torch.empty(N, dtype=torch.complex64, device="cuda")
+    sp = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        plan.forward(x.data_ptr(), y.data_ptr(), sp)
+        plan.adjoint(g.data_ptr(), gx.data_ptr(), sp)
+        torch.cuda.synchronize()
+        plan.status_poll()
+        lhs = sum(torch.vdot(g[o:o + N].to(torch.complex128), y[o:o + N].to(torch.complex128)).item()
+                  for o in range(0, plan.out_elems, N))
+        rhs = torch.vdot(gx.to(torch.complex128), x.to(torch.complex128)).item()
+        assert abs(lhs - rhs) <= 1e-5 * abs(lhs), (lhs, rhs)
+    del x, g, y, gx
+    torch.cuda.empty_cache()
 
 
 def test_adjoint_grad_workload(oracle):
