@@ -358,10 +358,14 @@ constexpr size_t adj_cols_smem(int E) {
 template <int QB>
 constexpr int adj_cols_e() { return kPassElemsLog; }
 constexpr size_t adj_rows_smem(int E, int CB) {
-  return (size_t)((1 << E) + twq_size(CB) + 4 * 65 + (1 << (E - 6)) + 16) * sizeof(float2);
+  return (size_t)((1 << E) + twq_size(CB) + (1 << (E - CB)) * 65 + (1 << (E - 6)) + 16) * sizeof(float2);
 }
 template <int CB>
 constexpr int adj_rows_e() { return rows_elems_log_c(CB, true); }
+// threads of a rows CTA of 2^E points
+constexpr int adj_rows_nt(int E, int CB) {
+  return E < kPassElemsLog ? kColsThreads : (E == kPassElemsLog ? (CB <= 10 ? kColsThreads : kPassThreads) : kPassThreadsWide);
+}
 
 // =============================================================== two-pass
 
@@ -376,12 +380,12 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
   constexpr int HU = (1 << CB) >> 6;
   constexpr int SH = E - kPassElemsLog;    // CTAs per item: 2^-SH (SH < 0), items per CTA: 2^SH
   // staging layout
-  constexpr int SA = CB <= 10 ? 5 : (CB <= 12 ? 6 : 3), SB = CB <= 10 ? 8 : 9;
+  constexpr int SA = (CB <= 10 && KCB == 2) ? 5 : (CB <= 12 ? 6 : 3), SB = (CB <= 10 && KCB == 2) ? 8 : 9;
   extern __shared__ __align__(1024) float2 sm[];
   float2* S = sm;                          // sequence j at j C (staging, then zlay)
   float2* TQ = sm + (1 << E);              // quarter-wave w_C
   float2* TWL = TQ + twq_size(CB);         // [KC][64] (row stride 65): w_h^(k2 t)
-  float2* TWH = TWL + 4 * 65;              // [KC][C/64] (row stride C/64 + 16/KC): w_h^(k2 64 u)
+  float2* TWH = TWL + KC * 65;             // [KC][C/64] (row stride C/64 + 16/KC): w_h^(k2 64 u)
   int item, blk;
   if constexpr (SH >= 0) {
     item = (int)blockIdx.x << SH;
@@ -631,14 +635,25 @@ void adj_cols_launch(const AdjArgs& a, int grid, cudaStream_t s) {
   constexpr int NT = E < kPassElemsLog ? kPassThreads : kColsThreads;
   k_adj_cols<NT, QB, E><<<grid << (kPassElemsLog - E), NT, adj_cols_smem(E), s>>>(a);
 }
+template <int E, int CB>
+void adj_rows_launch_e(const AdjArgs& a, int grid, cudaStream_t s) {
+  constexpr int NT = adj_rows_nt(E, CB);
+  // a CTA of 2^E points takes 2^(E-13) items (E >= 13) or half an item
+  const int g = E >= kPassElemsLog ? grid >> (E - kPassElemsLog) : grid << (kPassElemsLog - E);
+  if (a.t)
+    k_adj_rows<E, NT, CB, true><<<g, NT, adj_rows_smem(E, CB), s>>>(a);
+  else
+    k_adj_rows<E, NT, CB, false><<<g, NT, adj_rows_smem(E, CB), s>>>(a);
+}
 template <int CB>
 void adj_rows_launch(const AdjArgs& a, int grid, cudaStream_t s) {
-  constexpr int E = adj_rows_e<CB>();
-  constexpr int NT = E < kPassElemsLog ? kColsThreads : (E == kPassElemsLog ? kPassThreads : kPassThreadsWide);
-  if (a.t)
-    k_adj_rows<E, NT, CB, true><<<rows_grid(a.level, true, grid), NT, adj_rows_smem(E, CB), s>>>(a);
-  else
-    k_adj_rows<E, NT, CB, false><<<rows_grid(a.level, true, grid), NT, adj_rows_smem(E, CB), s>>>(a);
+  if constexpr (CB == 10) {
+    if (a.rows13) {
+      adj_rows_launch_e<kPassElemsLog, CB>(a, grid, s);
+      return;
+    }
+  }
+  adj_rows_launch_e<adj_rows_e<CB>(), CB>(a, grid, s);
 }
 template <int QB>
 cudaError_t adj_cols_attr() {
@@ -647,10 +662,9 @@ cudaError_t adj_cols_attr() {
   return cudaFuncSetAttribute(k_adj_cols<NT, QB, E>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)adj_cols_smem(E));
 }
-template <int CB>
+template <int CB, int E = adj_rows_e<CB>()>
 cudaError_t adj_rows_attr() {
-  constexpr int E = adj_rows_e<CB>();
-  constexpr int NT = E < kPassElemsLog ? kColsThreads : (E == kPassElemsLog ? kPassThreads : kPassThreadsWide);
+  constexpr int NT = adj_rows_nt(E, CB);
   cudaError_t e = cudaFuncSetAttribute(k_adj_rows<E, NT, CB, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)adj_rows_smem(E, CB));
   if (e == cudaSuccess)
@@ -689,6 +703,7 @@ cudaError_t set_adj_attributes() {
   static_for_host<10, 15>([&](auto C) {
     if (e == cudaSuccess) e = adj_rows_attr<decltype(C)::value>();
   });
+  if (e == cudaSuccess) e = adj_rows_attr<10, kPassElemsLog>();
   return e;
 }
 

@@ -53,7 +53,8 @@ constexpr int kPassThreads = 256;        // 2^13-point rows / adjoint cols CTAs
 constexpr int kColsThreads = 512;        // forward cols and 2^12-point adjoint rows CTAs (64 registers)
 constexpr int kPassThreadsWide = 512;    // the 2^14-point rows CTA (level 26)
 __host__ __device__ constexpr int cols_log(int i, bool) { return (i - 1) - 11 > 10 ? (i - 1) - 11 : 10; }
-// rows CTA size: 2^12 points for the adjoint's C = 2^10, else 2^13 (2^14 for C = 2^14)
+// rows CTA size: 2^13 points (2^14 for C = 2^14); for the adjoint's C = 2^10
+// it gives the 2^12-point CTAs taken when AdjArgs.rows13 = 0 (2^13 otherwise)
 __host__ __device__ constexpr int rows_elems_log_c(int cb, bool adj) {
   return (adj && cb <= 10) ? 12 : (cb > 13 ? cb : 13);
 }
@@ -95,6 +96,7 @@ struct AdjArgs {
   float2* acc;         // x_bar contributions of the large levels (N per signal)
   float2* scratch;     // two-pass levels intermediate (N/2 per signal)
   float2* scratch2;    // dual-level cols: the upper level's intermediate
+  int rows13;          // C = 2^10 rows CTAs of 2^13 points (8 residues) instead of 2^12
   int first;           // 1 when this is the top level (no e_in, acc written not added)
   Twiddles tw;
   int* status;

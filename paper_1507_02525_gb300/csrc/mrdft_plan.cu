@@ -113,6 +113,7 @@ struct mrdft_plan_s {
   bool seg_fixed = false;      // set by mrdft_plan_opts (else the environment may override)
   bool streams_fixed = false;
   bool dual_cols = true;       // pair two-pass levels in one cols pass (MRDFT_DUAL_COLS=0: off)
+  int adj_rows13 = 1;          // adjoint C = 2^10 rows CTAs of 2^13 points (MRDFT_ADJ_ROWS13=0: 2^12)
   int fwd_cb_min = 10;         // forward two-pass levels: C = 2^max(i - 12, fwd_cb_min) (MRDFT_FWD_CB=11)
   std::vector<cudaStream_t> workers;
   std::vector<cudaEvent_t> ev_join;
@@ -304,6 +305,8 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
   {
     const char* env = getenv("MRDFT_DUAL_COLS");
     if (env) p->dual_cols = atoi(env) != 0;
+    env = getenv("MRDFT_ADJ_ROWS13");
+    if (env) p->adj_rows13 = atoi(env) != 0;
     env = getenv("MRDFT_FWD_CB");
     if (env) p->fwd_cb_min = atoi(env) == 11 ? 11 : 10;
   }
@@ -633,6 +636,7 @@ mrdft_status launch_adj(mrdft_plan_s* p, AdjArgs a, const Launch& L, cudaStream_
 
 mrdft_status enqueue_adjoint(mrdft_plan_s* p, const void* gy, void* gx, cudaStream_t st) {
   AdjArgs a{};
+  a.rows13 = p->adj_rows13;
   a.gy = reinterpret_cast<const float2*>(gy);
   a.gx = reinterpret_cast<float2*>(gx);
   a.sigs = p->d_sigs;

@@ -371,6 +371,20 @@ def test_adjoint_long_signal_segments(oracle, seg_log):
             check_adjoint(gx[s], refs[s], gys[s], f"S={seg_log} rep={rep} s={s}")
 
 
+@pytest.mark.parametrize("rows13", ["0", "1"])
+@pytest.mark.parametrize("m", [15, 18, 20])
+def test_adjoint_rows_split(oracle, monkeypatch, rows13, m):
+    """Adjoint rows CTAs of 2^12 points (4 residues) or 2^13 (8 residues) for C = 2^10."""
+    monkeypatch.setenv("MRDFT_ADJ_ROWS13", rows13)
+    N = 1 << m
+    plan = _lib.Plan([N], 2)
+    gy = inputs.complex_signals(1, plan.out_elems, seed=400 + m)[0]
+    gx = run_adjoint(plan, gy)
+    for s in range(2):
+        g = gy[s * m * N:(s + 1) * m * N].reshape(m, N)
+        check_adjoint(gx[s * N:(s + 1) * N], oracle.adjoint(g.astype(np.complex128)), g, f"rows13={rows13} m={m} s={s}")
+
+
 def test_adjoint_dot_product_16m():
     """<M x, g> = <x, M^H g> at N = 2^24 with the default execution shape
     (two segments of 2^23 under one top level), sums in FP64 on the GPU."""
