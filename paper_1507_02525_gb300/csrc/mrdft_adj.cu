@@ -369,7 +369,7 @@ constexpr int adj_rows_nt(int E, int CB) {
 
 // =============================================================== two-pass
 
-// Adjoint of the forward two-pass level (h = Q * C, C = 2^cols_log(i)).
+// Adjoint of the forward two-pass level (h = Q * C).
 // rows: a CTA of 2^E points covers residues k2 in [k0, k0 + KC), KC = 2^E / C:
 //   odd-bin gradients at k = Q k1 + k2 -> IDFT_C over k1 -> times
 //   conj(w_h^(r k2)) -> scratch U[window][k2][r]; even bins -> e_out.
@@ -380,7 +380,7 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
   constexpr int HU = (1 << CB) >> 6;
   constexpr int SH = E - kPassElemsLog;    // CTAs per item: 2^-SH (SH < 0), items per CTA: 2^SH
   // staging layout
-  constexpr int SA = (CB <= 10 && KCB == 2) ? 5 : (CB <= 12 ? 6 : 3), SB = (CB <= 10 && KCB == 2) ? 8 : 9;
+  constexpr int SA = (CB <= 10 && KCB == 2) ? 5 : ((CB <= 12 && KCB != 4) ? 6 : 3), SB = (CB <= 10 && KCB == 2) ? 8 : 9;
   extern __shared__ __align__(1024) float2 sm[];
   float2* S = sm;                          // sequence j at j C (staging, then zlay)
   float2* TQ = sm + (1 << E);              // quarter-wave w_C
@@ -526,11 +526,10 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_adj_cols(cons
 //   j = 0: c1[q] + c0_0[q]        j = 1: c1[q + Q] - c0_0[q]
 //   j = 2: -c1[q] + c0_1[q]       j = 3: -c1[q + Q] - c0_1[q]
 // (the parent's halves a, b and each child's halves), read and written once.
-template <int QB>
+template <int QB, int CB>
 __global__ void __launch_bounds__(kColsThreads, 2) k_adj_cols2(const AdjArgs a) {
   constexpr int NT = kColsThreads;
   constexpr int E = kPassElemsLog;
-  constexpr int CB = 10;
   constexpr int Q = 1 << QB;
   constexpr int RCB = E - QB - 2, RC = 1 << RCB;
   constexpr int PTS = (1 << (E - 1)) / NT;               // FFT points per thread, each level
@@ -647,8 +646,8 @@ void adj_rows_launch_e(const AdjArgs& a, int grid, cudaStream_t s) {
 }
 template <int CB>
 void adj_rows_launch(const AdjArgs& a, int grid, cudaStream_t s) {
-  if constexpr (CB == 10) {
-    if (a.rows13) {
+  if constexpr (CB <= 10) {
+    if (a.rows13 || CB < 10) {
       adj_rows_launch_e<kPassElemsLog, CB>(a, grid, s);
       return;
     }
@@ -695,15 +694,18 @@ cudaError_t set_adj_attributes() {
   static_for_host<4, 12>([&](auto Q) {
     if (e == cudaSuccess) e = adj_cols_attr<decltype(Q)::value>();
   });
-  static_for_host<4, 10>([&](auto Q) {
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_adj_cols2<decltype(Q)::value>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)adj_cols2_smem());
+  static_for_host<9, 11>([&](auto C) {
+    static_for_host<4, 10>([&](auto Q) {
+      if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_adj_cols2<decltype(Q)::value, decltype(C)::value>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj_cols2_smem());
+    });
   });
   static_for_host<10, 15>([&](auto C) {
     if (e == cudaSuccess) e = adj_rows_attr<decltype(C)::value>();
   });
   if (e == cudaSuccess) e = adj_rows_attr<10, kPassElemsLog>();
+  if (e == cudaSuccess) e = adj_rows_attr<9, kPassElemsLog>();
   return e;
 }
 
@@ -730,27 +732,34 @@ cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s) {
         : k_adj_window<13, false><<<grid, kWinThreads, kAdjWinSmem, s>>>(a);
   return cudaGetLastError();
 }
+// C = 2^adj_cb of a two-pass level (Q = h / C <= 2^11 keeps cols chunks of >= 4)
+static int adj_cb(int cb_min, int i) {
+  const int m = cb_min ? cb_min : 10;
+  return (i - 1) - 11 > m ? (i - 1) - 11 : m;
+}
 cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s) {
-  const int CB = cols_log(a.level, true);
-  static_for_host<10, 15>([&](auto C) {
+  const int CB = adj_cb(a.cb_min, a.level);
+  static_for_host<9, 15>([&](auto C) {
     if (CB == decltype(C)::value) adj_rows_launch<decltype(C)::value>(a, grid, s);
   });
   return cudaGetLastError();
 }
-bool adj_cols2_pairable(int upper_level) {
-  const int i = upper_level - 1;
-  return i >= 15 && cols_log(i, true) == 10 && cols_log(upper_level, true) == 10 && i - 11 >= 4 && i - 11 <= 9;
+bool adj_cols2_pairable(int upper_level, int cb_min) {
+  const int i = upper_level - 1, CB = adj_cb(cb_min, i), QB = (i - 1) - CB;
+  return i >= 15 && adj_cb(cb_min, upper_level) == CB && (CB == 9 || CB == 10) && QB >= 4 && QB <= 9;
 }
 cudaError_t launch_adj_cols2(const AdjArgs& a, int grid, cudaStream_t s) {
-  const int QB = (a.level - 1) - 11;
-  static_for_host<4, 10>([&](auto Q) {
-    constexpr int q = decltype(Q)::value;
-    if (QB == q) k_adj_cols2<q><<<grid << 1, kColsThreads, adj_cols2_smem(), s>>>(a);
+  const int i = a.level - 1, CB = adj_cb(a.cb_min, i), QB = (i - 1) - CB;
+  static_for_host<9, 11>([&](auto C) {
+    static_for_host<4, 10>([&](auto Q) {
+      constexpr int q = decltype(Q)::value, c = decltype(C)::value;
+      if (QB == q && CB == c) k_adj_cols2<q, c><<<grid << 1, kColsThreads, adj_cols2_smem(), s>>>(a);
+    });
   });
   return cudaGetLastError();
 }
 cudaError_t launch_adj_cols(const AdjArgs& a, int grid, cudaStream_t s) {
-  const int QB = (a.level - 1) - cols_log(a.level, true);
+  const int QB = (a.level - 1) - adj_cb(a.cb_min, a.level);
   static_for_host<4, 12>([&](auto Q) {
     if (QB == decltype(Q)::value) adj_cols_launch<decltype(Q)::value>(a, grid, s);
   });

@@ -55,7 +55,7 @@ struct TwQ {
 };
 __device__ __forceinline__ int twq_pad(int r) { return r + (r >> 4) + (r >> 8); }
 __host__ __device__ constexpr int twq_size(int TB) {
-  return (1 << (TB - 2)) + (1 << (TB - 6)) + (1 << (TB - 10)) + 1;
+  return (1 << (TB - 2)) + (TB >= 6 ? 1 << (TB - 6) : 0) + (TB >= 10 ? 1 << (TB - 10) : 0) + 1;
 }
 __device__ __forceinline__ float2 twq(const TwQ& t, int e) {
   const int qb = t.TB - 2;

@@ -316,7 +316,7 @@ constexpr size_t rows_smem(int E, int CB) {
 
 // =============================================================== two-pass
 
-// Level i with h = 2^(i-1) = Q * C, C = 2^CB (cols_log), Q = 2^QB.
+// Level i with h = 2^(i-1) = Q * C, C = 2^CB (fwd_cb), Q = 2^QB.
 // With n = r + C q (r < C, q < Q) and k = Q k1 + k2:
 //   DFT_h(z)[Q k1 + k2] = sum_r w_C^(r k1) w_h^(r k2) sum_q z[r + C q] w_Q^(q k2).
 // cols: item (sig, window, c) covers chunk offsets r in [r0, r0 + RC),
@@ -591,10 +591,10 @@ cudaError_t set_fwd_attributes() {
   static_for_host<3, 12>([&](auto Q) {
     if (e == cudaSuccess) e = cols_attr<decltype(Q)::value>();
   });
-  static_for_host<10, 15>([&](auto C) {
+  static_for_host<9, 15>([&](auto C) {
     if (e == cudaSuccess) e = rows_attr<decltype(C)::value>();
   });
-  static_for_host<10, 12>([&](auto C) {
+  static_for_host<9, 12>([&](auto C) {
     static_for_host<3, 10>([&](auto Q) {
       if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_fwd_cols2<decltype(Q)::value, decltype(C)::value>,
@@ -633,11 +633,11 @@ cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s) {
 }
 bool fwd_cols2_pairable(int upper_level, int cb_min) {
   const int i = upper_level - 1, CB = fwd_cb(cb_min, i), QB = (i - 1) - CB;
-  return i >= 15 && fwd_cb(cb_min, upper_level) == CB && (CB == 10 || CB == 11) && QB >= 3 && QB <= 9;
+  return i >= 15 && fwd_cb(cb_min, upper_level) == CB && CB >= 9 && CB <= 11 && QB >= 3 && QB <= 9;
 }
 cudaError_t launch_fwd_cols2(const FwdArgs& a, int grid, cudaStream_t s) {
   const int i = a.level - 1, CB = fwd_cb(a.cb_min, i), QB = (i - 1) - CB;
-  static_for_host<10, 12>([&](auto C) {
+  static_for_host<9, 12>([&](auto C) {
     static_for_host<3, 10>([&](auto Q) {
       constexpr int q = decltype(Q)::value, c = decltype(C)::value;
       if (QB == q && CB == c) k_fwd_cols2<q, c><<<grid << 1, kColsThreads, cols2_smem(), s>>>(a);
@@ -647,7 +647,7 @@ cudaError_t launch_fwd_cols2(const FwdArgs& a, int grid, cudaStream_t s) {
 }
 cudaError_t launch_fwd_rows(const FwdArgs& a, int grid, cudaStream_t s) {
   const int CB = fwd_cb(a.cb_min, a.level);
-  static_for_host<10, 15>([&](auto C) {
+  static_for_host<9, 15>([&](auto C) {
     if (CB == decltype(C)::value) rows_launch<decltype(C)::value>(a, grid, s);
   });
   return cudaGetLastError();

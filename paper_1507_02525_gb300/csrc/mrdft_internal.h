@@ -42,30 +42,25 @@ constexpr int kTile = 1 << kTileLog;         // 4096 samples per tile
 constexpr int kTileThreads = 256;            // 16 samples per thread, 2 CTAs per SM
 constexpr int kWinMaxLog = 13;               // one CTA FFT holds up to 2^13 points
 constexpr int kWinThreads = 256;             // levels 13, 14: 16 or 32 points per thread
-// Two-pass levels (i >= 15), h = 2^(i-1) = Q * C with C = 2^cols_log(i):
-//   2^10 up to level 22, then 2^(i-12), so that Q <= 2^11 and every cols CTA
-//   reads chunks of at least 4 consecutive samples (the forward can take
-//   C = 2^11 up to level 23 instead: FwdArgs.cb_min).
-//   cols pass: 2^13 points per CTA (RC = 2^13 / Q chunk offsets), 2 CTAs/SM
-//   rows pass: 2^rows_elems_log(i) points per CTA (KC = 2^E / C residues).
+// Two-pass levels (i >= 15), h = 2^(i-1) = Q * C with C = 2^max(i - 12, cb_min),
+//   so that Q <= 2^11 and every cols CTA reads chunks of at least 4
+//   consecutive samples; cb_min is 9 for the forward and 10 for the adjoint
+//   (FwdArgs / AdjArgs.cb_min; both directions accept 9 and 10, the forward
+//   also 11).
+//   cols pass: 2^12 or 2^13 points per CTA (RC chunk offsets x Q)
+//   rows pass: 2^E points per CTA (KC = 2^E / C residues), E = rows_elems_log_c.
 constexpr int kPassElemsLog = 13;
 constexpr int kPassThreads = 256;        // 2^13-point rows / adjoint cols CTAs
 constexpr int kColsThreads = 512;        // forward cols and 2^12-point adjoint rows CTAs (64 registers)
 constexpr int kPassThreadsWide = 512;    // the 2^14-point rows CTA (level 26)
-__host__ __device__ constexpr int cols_log(int i, bool) { return (i - 1) - 11 > 10 ? (i - 1) - 11 : 10; }
-// rows CTA size: 2^13 points (2^14 for C = 2^14); for the adjoint's C = 2^10
+// rows CTA size: 2^13 points (2^14 for C = 2^14); for the adjoint's C <= 2^10
 // it gives the 2^12-point CTAs taken when AdjArgs.rows13 = 0 (2^13 otherwise)
 __host__ __device__ constexpr int rows_elems_log_c(int cb, bool adj) {
   return (adj && cb <= 10) ? 12 : (cb > 13 ? cb : 13);
 }
-__host__ __device__ constexpr int rows_elems_log(int i, bool adj) { return rows_elems_log_c(cols_log(i, adj), adj); }
 // work items of a two-pass level, per window: one per cols CTA (2^(i-14));
 // a rows CTA of 2^E points takes 2^(E-13) items (E >= 13) or half an item
 __host__ __device__ constexpr int pass_items(int i) { return 1 << ((i - 1) - kPassElemsLog); }
-__host__ __device__ constexpr int rows_grid(int i, bool adj, int items) {
-  return rows_elems_log(i, adj) >= kPassElemsLog ? items >> (rows_elems_log(i, adj) - kPassElemsLog)
-                                                 : items << (kPassElemsLog - rows_elems_log(i, adj));
-}
 
 struct FwdArgs {
   const void* x;  // float2* (complex64) or float* (real FP32)
@@ -78,7 +73,7 @@ struct FwdArgs {
   int level;          // large-level kernels: level i being built
   float2* scratch;    // two-pass levels: intermediate, N/2 per signal
   float2* scratch2;   // dual-level cols: the upper level's intermediate
-  int cb_min;         // two-pass levels: C = 2^max(i - 12, cb_min), cb_min 10 or 11 (0 means 10)
+  int cb_min;         // two-pass levels: C = 2^max(i - 12, cb_min), cb_min 9..11 (0 means 10)
   Twiddles tw;
   int* status;
 };
@@ -97,6 +92,7 @@ struct AdjArgs {
   float2* scratch;     // two-pass levels intermediate (N/2 per signal)
   float2* scratch2;    // dual-level cols: the upper level's intermediate
   int rows13;          // C = 2^10 rows CTAs of 2^13 points (8 residues) instead of 2^12
+  int cb_min;          // two-pass levels: C = 2^max(i - 12, cb_min), cb_min 9 or 10 (0 means 10)
   int first;           // 1 when this is the top level (no e_in, acc written not added)
   Twiddles tw;
   int* status;
@@ -127,7 +123,7 @@ cudaError_t launch_adj_cols(const AdjArgs& a, int grid, cudaStream_t s);
 // update of acc; grid = level-a.level items; needs cols_log(., adj) == 10 and
 // a.level - 12 in [4, 9]
 cudaError_t launch_adj_cols2(const AdjArgs& a, int grid, cudaStream_t s);
-bool adj_cols2_pairable(int upper_level);
+bool adj_cols2_pairable(int upper_level, int cb_min);
 
 cudaError_t set_kernel_attributes();
 

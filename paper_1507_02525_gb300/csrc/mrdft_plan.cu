@@ -114,7 +114,8 @@ struct mrdft_plan_s {
   bool streams_fixed = false;
   bool dual_cols = true;       // pair two-pass levels in one cols pass (MRDFT_DUAL_COLS=0: off)
   int adj_rows13 = 1;          // adjoint C = 2^10 rows CTAs of 2^13 points (MRDFT_ADJ_ROWS13=0: 2^12)
-  int fwd_cb_min = 10;         // forward two-pass levels: C = 2^max(i - 12, fwd_cb_min) (MRDFT_FWD_CB=11)
+  int adj_cb_min = 10;         // adjoint two-pass levels: C = 2^max(i - 12, adj_cb_min) (MRDFT_ADJ_CB)
+  int fwd_cb_min = 9;          // forward two-pass levels: C = 2^max(i - 12, fwd_cb_min) (MRDFT_FWD_CB=10, 11)
   std::vector<cudaStream_t> workers;
   std::vector<cudaEvent_t> ev_join;
   cudaEvent_t ev_fork = nullptr;
@@ -307,8 +308,10 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     if (env) p->dual_cols = atoi(env) != 0;
     env = getenv("MRDFT_ADJ_ROWS13");
     if (env) p->adj_rows13 = atoi(env) != 0;
+    env = getenv("MRDFT_ADJ_CB");
+    if (env) p->adj_cb_min = std::max(9, std::min(10, atoi(env)));
     env = getenv("MRDFT_FWD_CB");
-    if (env) p->fwd_cb_min = atoi(env) == 11 ? 11 : 10;
+    if (env) p->fwd_cb_min = std::max(9, std::min(11, atoi(env)));
   }
   const int S = p->seg_log;
   const int64_t in_b = p->dtype == MRDFT_R32 ? 4 : 8;
@@ -614,7 +617,7 @@ mrdft_status launch_adj(mrdft_plan_s* p, AdjArgs a, const Launch& L, cudaStream_
     // which runs it with its own after both rows passes
     a.scratch = p->d_scratch + (L.level & 1) * p->half_elems;
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_ROWS, L.bytes, st, [&] { return launch_adj_rows(a, L.count, st); }));
-    if (L.dual == 1 && adj_cols2_pairable(L.level + 1)) {
+    if (L.dual == 1 && adj_cols2_pairable(L.level + 1, p->adj_cb_min)) {
       AdjArgs d = a;
       d.level = L.level + 1;
       d.nitems = L.c2_count;
@@ -627,7 +630,7 @@ mrdft_status launch_adj(mrdft_plan_s* p, AdjArgs a, const Launch& L, cudaStream_
         t.items = p->d_levels + L.tail_off;
         MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_COLS, 0, st, [&] { return launch_adj_cols(t, L.tail_count, st); }));
       }
-    } else if (!(L.dual == 2 && adj_cols2_pairable(L.level))) {
+    } else if (!(L.dual == 2 && adj_cols2_pairable(L.level, p->adj_cb_min))) {
       MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_COLS, 0, st, [&] { return launch_adj_cols(a, L.count, st); }));
     }
   }
@@ -637,6 +640,7 @@ mrdft_status launch_adj(mrdft_plan_s* p, AdjArgs a, const Launch& L, cudaStream_
 mrdft_status enqueue_adjoint(mrdft_plan_s* p, const void* gy, void* gx, cudaStream_t st) {
   AdjArgs a{};
   a.rows13 = p->adj_rows13;
+  a.cb_min = p->adj_cb_min;
   a.gy = reinterpret_cast<const float2*>(gy);
   a.gx = reinterpret_cast<float2*>(gx);
   a.sigs = p->d_sigs;
@@ -851,8 +855,8 @@ mrdft_status mrdft_plan_info(mrdft_plan_t p, int32_t* tile_log, int32_t* fwd_lau
   int na = n;
   auto count = [&](const Launch& L) {
     if (L.kind != LK_PASS) na += 1;
-    else if (L.dual == 1 && adj_cols2_pairable(L.level + 1)) na += 2 + (L.tail_count ? 1 : 0);
-    else na += L.dual == 2 && adj_cols2_pairable(L.level) ? 1 : 2;
+    else if (L.dual == 1 && adj_cols2_pairable(L.level + 1, p->adj_cb_min)) na += 2 + (L.tail_count ? 1 : 0);
+    else na += L.dual == 2 && adj_cols2_pairable(L.level, p->adj_cb_min) ? 1 : 2;
     if (L.kind != LK_PASS) n += 1;
     else if (L.dual == 1) n += 2 + (L.tail_count ? 1 : 0);
     else n += L.dual == 2 ? 1 : 2;

@@ -138,7 +138,7 @@ def test_forward_dual_cols_ragged(oracle, monkeypatch, seg_log, dual):
         check_forward_levels(ys_, ref, xs, f"dual={dual} S={seg_log} s={s} N={len(xs)}")
 
 
-@pytest.mark.parametrize("cb", ["10", "11"])
+@pytest.mark.parametrize("cb", ["9", "10", "11"])
 @pytest.mark.parametrize("m", [15, 16, 19, 22])
 def test_forward_two_pass_split(oracle, monkeypatch, cb, m):
     """Both splits of the two-pass levels, h = Q C with C = 2^max(i - 12, cb)."""
@@ -371,10 +371,12 @@ def test_adjoint_long_signal_segments(oracle, seg_log):
             check_adjoint(gx[s], refs[s], gys[s], f"S={seg_log} rep={rep} s={s}")
 
 
-@pytest.mark.parametrize("rows13", ["0", "1"])
+@pytest.mark.parametrize("cb,rows13", [("10", "0"), ("10", "1"), ("9", "1")])
 @pytest.mark.parametrize("m", [15, 18, 20])
-def test_adjoint_rows_split(oracle, monkeypatch, rows13, m):
-    """Adjoint rows CTAs of 2^12 points (4 residues) or 2^13 (8 residues) for C = 2^10."""
+def test_adjoint_rows_split(oracle, monkeypatch, cb, rows13, m):
+    """Adjoint splits h = Q C with C = 2^max(i - 12, cb): rows CTAs of 2^12
+    points (4 residues) or 2^13 (8 residues) for C = 2^10, 2^13 for C = 2^9."""
+    monkeypatch.setenv("MRDFT_ADJ_CB", cb)
     monkeypatch.setenv("MRDFT_ADJ_ROWS13", rows13)
     N = 1 << m
     plan = _lib.Plan([N], 2)
@@ -382,7 +384,7 @@ def test_adjoint_rows_split(oracle, monkeypatch, rows13, m):
     gx = run_adjoint(plan, gy)
     for s in range(2):
         g = gy[s * m * N:(s + 1) * m * N].reshape(m, N)
-        check_adjoint(gx[s * N:(s + 1) * N], oracle.adjoint(g.astype(np.complex128)), g, f"rows13={rows13} m={m} s={s}")
+        check_adjoint(gx[s * N:(s + 1) * N], oracle.adjoint(g.astype(np.complex128)), g, f"C=2^{cb} rows13={rows13} m={m} s={s}")
 
 
 def test_adjoint_dot_product_16m():
