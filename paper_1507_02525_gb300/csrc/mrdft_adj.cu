@@ -638,7 +638,9 @@ template <int E, int CB>
 void adj_rows_launch_e(const AdjArgs& a, int grid, cudaStream_t s) {
   constexpr int NT = adj_rows_nt(E, CB);
   // a CTA of 2^E points takes 2^(E-13) items (E >= 13) or half an item
-  const int g = E >= kPassElemsLog ? grid >> (E - kPassElemsLog) : grid << (kPassElemsLog - E);
+  int g;
+  if constexpr (E >= kPassElemsLog) g = grid >> (E - kPassElemsLog);
+  else g = grid << (kPassElemsLog - E);
   if (a.t)
     k_adj_rows<E, NT, CB, true><<<g, NT, adj_rows_smem(E, CB), s>>>(a);
   else

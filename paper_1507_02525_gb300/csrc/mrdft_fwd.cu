@@ -554,12 +554,24 @@ void cols_launch(const FwdArgs& a, int grid, cudaStream_t s) {
 }
 template <int CB>
 constexpr int rows_e() { return rows_elems_log_c(CB, false); }
+template <int CB, int E = rows_e<CB>()>
+void rows_launch_e(const FwdArgs& a, int grid, cudaStream_t s) {
+  constexpr int NT = E < kPassElemsLog ? kPassThreads : (E == kPassElemsLog ? kColsThreads : kPassThreadsWide);
+  // a CTA of 2^E points takes 2^(E-13) items (E >= 13) or half an item
+  int g;
+  if constexpr (E >= kPassElemsLog) g = grid >> (E - kPassElemsLog);
+  else g = grid << (kPassElemsLog - E);
+  k_fwd_rows<E, NT, CB><<<g, NT, rows_smem(E, CB), s>>>(a);
+}
 template <int CB>
 void rows_launch(const FwdArgs& a, int grid, cudaStream_t s) {
-  constexpr int E = rows_e<CB>();
-  constexpr int NT = E < kPassElemsLog ? kPassThreads : (E == kPassElemsLog ? kColsThreads : kPassThreadsWide);
-  // a CTA of 2^E points takes 2^(E-13) items (E >= 13)
-  k_fwd_rows<E, NT, CB><<<grid >> (E - kPassElemsLog), NT, rows_smem(E, CB), s>>>(a);
+  if constexpr (CB == 12) {
+    if (a.rows14) {
+      rows_launch_e<CB, 14>(a, grid, s);
+      return;
+    }
+  }
+  rows_launch_e<CB>(a, grid, s);
 }
 template <int QB>
 cudaError_t cols_attr() {
@@ -567,9 +579,8 @@ cudaError_t cols_attr() {
   constexpr int NT = E < kPassElemsLog ? kPassThreads : kColsThreads;
   return cudaFuncSetAttribute(k_fwd_cols<NT, QB, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cols_smem(E));
 }
-template <int CB>
+template <int CB, int E = rows_e<CB>()>
 cudaError_t rows_attr() {
-  constexpr int E = rows_e<CB>();
   constexpr int NT = E < kPassElemsLog ? kPassThreads : (E == kPassElemsLog ? kColsThreads : kPassThreadsWide);
   return cudaFuncSetAttribute(k_fwd_rows<E, NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               (int)rows_smem(E, CB));
@@ -594,6 +605,7 @@ cudaError_t set_fwd_attributes() {
   static_for_host<9, 15>([&](auto C) {
     if (e == cudaSuccess) e = rows_attr<decltype(C)::value>();
   });
+  if (e == cudaSuccess) e = rows_attr<12, 14>();
   static_for_host<9, 12>([&](auto C) {
     static_for_host<3, 10>([&](auto Q) {
       if (e == cudaSuccess)

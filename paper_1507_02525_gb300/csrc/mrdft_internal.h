@@ -74,6 +74,7 @@ struct FwdArgs {
   float2* scratch;    // two-pass levels: intermediate, N/2 per signal
   float2* scratch2;   // dual-level cols: the upper level's intermediate
   int cb_min;         // two-pass levels: C = 2^max(i - 12, cb_min), cb_min 9..11 (0 means 10)
+  int rows14;         // C = 2^12 rows CTAs of 2^14 points (4 residues, 1 per SM) instead of 2^13
   Twiddles tw;
   int* status;
 };

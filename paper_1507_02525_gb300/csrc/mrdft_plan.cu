@@ -115,6 +115,7 @@ struct mrdft_plan_s {
   bool dual_cols = true;       // pair two-pass levels in one cols pass (MRDFT_DUAL_COLS=0: off)
   int adj_rows13 = 1;          // adjoint C = 2^10 rows CTAs of 2^13 points (MRDFT_ADJ_ROWS13=0: 2^12)
   int adj_cb_min = 10;         // adjoint two-pass levels: C = 2^max(i - 12, adj_cb_min) (MRDFT_ADJ_CB)
+  int fwd_rows14 = 1;          // forward C = 2^12 rows CTAs of 2^14 points (MRDFT_FWD_ROWS14=0: 2^13)
   int fwd_cb_min = 9;          // forward two-pass levels: C = 2^max(i - 12, fwd_cb_min) (MRDFT_FWD_CB=10, 11)
   std::vector<cudaStream_t> workers;
   std::vector<cudaEvent_t> ev_join;
@@ -310,6 +311,8 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     if (env) p->adj_rows13 = atoi(env) != 0;
     env = getenv("MRDFT_ADJ_CB");
     if (env) p->adj_cb_min = std::max(9, std::min(10, atoi(env)));
+    env = getenv("MRDFT_FWD_ROWS14");
+    if (env) p->fwd_rows14 = atoi(env) != 0;
     env = getenv("MRDFT_FWD_CB");
     if (env) p->fwd_cb_min = std::max(9, std::min(11, atoi(env)));
   }
@@ -568,6 +571,7 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
   a.sigs = p->d_sigs;
   a.scratch = p->d_scratch;
   a.cb_min = p->fwd_cb_min;
+  a.rows14 = p->fwd_rows14;
   a.tw = twiddles(p);
   a.status = p->d_status;
   if (p->n_tiny) {

@@ -141,7 +141,7 @@ def test_forward_dual_cols_ragged(oracle, monkeypatch, seg_log, dual):
 @pytest.mark.parametrize("cb", ["9", "10", "11"])
 @pytest.mark.parametrize("m", [15, 16, 19, 22])
 def test_forward_two_pass_split(oracle, monkeypatch, cb, m):
-    """Both splits of the two-pass levels, h = Q C with C = 2^max(i - 12, cb)."""
+    """The splits of the two-pass levels, h = Q C with C = 2^max(i - 12, cb)."""
     monkeypatch.setenv("MRDFT_FWD_CB", cb)
     N = 1 << m
     x = inputs.complex_signals(1, N, seed=300 + m)[0]
@@ -243,6 +243,27 @@ def test_single_16m_every_level(oracle, big_signal):
         rel = np.linalg.norm(d) / np.linalg.norm(ref)
         assert rel <= 2e-6 * i, f"level {i}: rel {rel:.3e}"
         assert np.abs(d).max() <= 1e-5 * xn, f"level {i}: max abs"
+
+
+def test_single_16m_top_rows_variant(oracle, big_signal, monkeypatch):
+    """Level 24 (C = 2^12) with rows CTAs of 2^13 points instead of 2^14."""
+    monkeypatch.setenv("MRDFT_FWD_ROWS14", "0")
+    x, _ = big_signal
+    plan = _lib.Plan([1 << 24], 1)
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty(plan.out_elems, dtype=torch.complex64, device="cuda")
+    plan.forward(xt.data_ptr(), y.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    plan.status_poll()
+    x128 = x.astype(np.complex128)
+    xn = float(np.linalg.norm(x128))
+    for i in (23, 24):
+        ref = oracle.forward_level(x128, i)
+        d = y.view(24, 1 << 24)[i - 1].cpu().numpy().astype(np.complex128) - ref
+        assert np.linalg.norm(d) / np.linalg.norm(ref) <= 2e-6 * i, f"level {i}"
+        assert np.abs(d).max() <= 1e-5 * xn, f"level {i} max abs"
+    del y, xt
+    torch.cuda.empty_cache()
 
 
 def test_single_16m_sampled_bins(oracle, big_signal):
