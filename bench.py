@@ -391,12 +391,13 @@ def main():
         per_launch_ms = ms / n
         bytes_per_launch = b / n
         ach = bytes_per_launch / (per_launch_ms * 1e-3) / 1e9 if bytes_per_launch else 0.0
+        # DRAM bytes per launch of each part (profiles/ncu_traffic.txt), summed
+        # over the part's launches and spread over the unit's launches (a
+        # dual-level cols launch serves two rows launches)
         traffic = None
-        if len(parts) == 1:
-            traffic = ncu_traffic(name, args.workload + "_noseg")
-        else:
-            tr = [ncu_traffic(q, args.workload + "_noseg") for q in parts]
-            traffic = sum(tr) if all(t is not None for t in tr) else None
+        tr = [ncu_traffic(q, args.workload + "_noseg") for q in parts]
+        if all(t is not None for t in tr):
+            traffic = int(sum(t * kt[q][1] for t, q in zip(tr, parts)) / n)
         share = ms / sum(v[0] for v in kt.values())
         return {"bound": "hbm", "kernel": "+".join(f"k_{q}" for q in parts), "achieved": round(ach, 1),
                 "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4), "traffic": traffic,
