@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
   for (int c = tid; c < (Tn >> 1); c += NT) {
     const int e = c << 1;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (below) v = __ldcg(reinterpret_cast<const float4*>(a.acc + TS[0].x_base + e));
+    if (below) v = __ldcg(reinterpret_cast<const float4*>(a.acc + 2 * sd0.aux_off + ((int64_t)it.tile << tl) + e));
     st4s_a(ACC + swz128(e), v);
   }
 
@@ -305,7 +305,7 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) 
   const SigDesc sd = a.sigs[it.sig];
   const int64_t w = it.window;
   const bool add = sd.m > i;
-  float2* acc = a.acc + sd.in_off + (w << i);
+  float2* acc = a.acc + 2 * sd.aux_off + (w << i);
   load_twq<NT>(TQ, 13, a.tw);
   const float2 w1 = __ldg(&a.tw.tw13[1]);  // w_{2^14}
   float lsum = 0.f;  // fused loss: this thread's share
@@ -470,7 +470,7 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_adj_cols(cons
   const int64_t w = it.window;
   const int r0 = ((it.block << SH) | ((int)blockIdx.x & ((1 << SH) - 1))) << RCB;
   const float2* U = a.scratch + sd.aux_off + (w << HB);
-  float2* acc = a.acc + sd.in_off + (w << i);
+  float2* acc = a.acc + 2 * sd.aux_off + (w << i);
   const bool add = sd.m > i;
 #pragma unroll 1
   for (int t0 = 0; t0 < PTS; t0 += 8) {
@@ -550,7 +550,7 @@ __global__ void __launch_bounds__(kColsThreads, 2) k_adj_cols2(const AdjArgs a) 
   const int r0 = ((it.block << 1) | ((int)blockIdx.x & 1)) << RCB;
   const float2* U1 = a.scratch2 + sd.aux_off + (W << i);
   const float2* U0 = a.scratch + sd.aux_off + ((2 * W) << (i - 1));
-  float2* acc = a.acc + sd.in_off + (W << i1);
+  float2* acc = a.acc + 2 * sd.aux_off + (W << i1);
   const bool add = sd.m > i1;
   {
     float2 u1[PTS], u0[PTS];

@@ -12,7 +12,7 @@ namespace mrdft {
 struct SigDesc {
   int64_t in_off;   // first sample of the signal in x
   int64_t out_off;  // first output of level 1 in y; level i at out_off + (i-1) N
-  int64_t aux_off;  // first element of the signal in the per-signal scratch
+  int64_t aux_off;  // first element of the signal in the per-signal scratch (N/2 per signal of m > 12)
   int32_t m;        // log2 N
   int32_t pad;
 };
@@ -89,7 +89,7 @@ struct AdjArgs {
   int level;
   const float2* e_in;  // even-bin propagation from level+1 (N/2 per signal)
   float2* e_out;       // even-bin propagation to level-1 (N/2 per signal)
-  float2* acc;         // x_bar contributions of the large levels (N per signal)
+  float2* acc;         // x_bar contributions of the large levels (N per signal of m > 12, at 2 aux_off)
   float2* scratch;     // two-pass levels intermediate (N/2 per signal)
   float2* scratch2;    // dual-level cols: the upper level's intermediate
   int rows13;          // C = 2^10 rows CTAs of 2^13 points (8 residues) instead of 2^12

@@ -131,7 +131,7 @@ struct mrdft_plan_s {
   // parent window run on different worker streams, and each writes its own
   // lower levels' propagation into d_e0 / d_e1 over the parent's range
   float2* d_etop = nullptr;
-  float2* d_acc = nullptr;      // N per signal
+  float2* d_acc = nullptr;      // N per signal of m > 12, at 2 aux_off
   int* d_status = nullptr;
   void* d_stage_x = nullptr;
   void* d_stage_y = nullptr;

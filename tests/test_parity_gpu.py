@@ -363,6 +363,20 @@ def test_adjoint_dual_cols_ragged(oracle, monkeypatch, seg_log, dual):
         check_adjoint(gx[s], ref, gys[s], f"dual={dual} S={seg_log} s={s}")
 
 
+def test_adjoint_short_signals_first(oracle):
+    """Signals that end inside a tile ahead of longer ones: the accumulator of
+    the large levels holds only the longer signals and is indexed by their own
+    offsets, not by their position in x."""
+    lengths = [1 << 12] * 64 + [1 << 8] * 64 + [1 << 17] + [1 << 10] * 8 + [1 << 15]
+    plan = _lib.Plan(lengths, len(lengths))
+    gy = inputs.complex_signals(1, plan.out_elems, seed=93)[0]
+    gx = split_in(run_adjoint(plan, gy), lengths)
+    gys = split_out(gy, lengths)
+    for s in (0, 63, 64, 127, 128, 129, 136):
+        ref = oracle.adjoint(gys[s].astype(np.complex128))
+        check_adjoint(gx[s], ref, gys[s], f"short-first s={s} N={lengths[s]}")
+
+
 def test_adjoint_dot_product():
     """<M x, g> = <x, M^H g> with both sides on the GPU (N = 2^18, batch 4)."""
     B, N = 4, 1 << 18
