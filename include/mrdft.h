@@ -76,6 +76,12 @@ typedef enum {
  * Returns MRDFT_EINVAL for a bad length or count, MRDFT_ENOMEM / MRDFT_ECUDA
  * when allocation fails.  The plan is bound to the device current at the
  * call; it may be used from one stream at a time.
+ * Environment variables read here change only the speed, never the result:
+ * MRDFT_SEG_LOG, MRDFT_STREAMS (execution shape, see mrdft_plan_opts),
+ * MRDFT_DUAL_COLS=0 (one cols pass per two-pass level instead of one per
+ * pair), MRDFT_FWD_CB / MRDFT_ADJ_CB (two-pass split C = 2^max(i-12, cb);
+ * defaults 9 and 10), MRDFT_FWD_ROWS14=0 and MRDFT_ADJ_ROWS13=0 (smaller
+ * rows CTAs for the C = 2^12 forward and C <= 2^10 adjoint levels).
  */
 mrdft_status mrdft_plan(mrdft_plan_t* out, const int64_t* lengths, int64_t n_lengths,
                         int64_t batch, int dtype, uint32_t flags);
@@ -140,10 +146,10 @@ mrdft_status mrdft_plan_info(mrdft_plan_t plan, int32_t* tile_log, int32_t* fwd_
 
 /* Kernel kinds for per-kernel timing. */
 enum {
-  MRDFT_KIND_FWD_TILE = 0,   /* levels 1..13 of 8192-sample tiles (1..m for shorter signals) */
+  MRDFT_KIND_FWD_TILE = 0,   /* levels 1..12 of 4096-sample tiles (1..m for shorter signals) */
   MRDFT_KIND_FWD_TINY = 1,   /* signals of length <= 16 */
-  MRDFT_KIND_FWD_WINDOW = 2, /* level 14, one window per CTA */
-  MRDFT_KIND_FWD_COLS = 3,   /* two-pass levels, cross-chunk pass */
+  MRDFT_KIND_FWD_WINDOW = 2, /* level 13 or 14, one window per CTA */
+  MRDFT_KIND_FWD_COLS = 3,   /* two-pass levels, cross-chunk pass (one launch may serve two levels) */
   MRDFT_KIND_FWD_ROWS = 4,   /* two-pass levels, per-residue pass + even bins */
   MRDFT_KIND_ADJ_TILE = 5,
   MRDFT_KIND_ADJ_TINY = 6,
