@@ -10,7 +10,8 @@
 //
 //   k_adj_window / k_adj_rows + k_adj_cols : levels above the tile, top down;
 //     even-bin propagation to the next level in `e_out` (N/2 per signal),
-//     time-domain contributions accumulated in `acc` (N per signal).
+//     time-domain contributions accumulated in `acc` (N per signal);
+//     k_adj_cols2 does the cols passes of two consecutive levels at once.
 //   k_adj_tile : levels tlog..1 of a tile, adds `acc`, writes x_bar.
 // Every gradient-reading kernel has a FUSED variant (mrdft_loss_grad): gy then
 // holds Y, the upstream gradient of level i is 2^(1-i) (Y - T) computed on the
@@ -516,8 +517,8 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_adj_cols(cons
 }
 
 // Two levels, one update of the accumulated gradient: the cols passes of
-// levels i and i + 1 (both with C = 2^10, Q = 2^QB for level i and 2Q for
-// level i + 1), after both rows passes.  A CTA takes chunk offsets
+// levels i and i + 1 (the same C, Q = 2^QB for level i and 2Q for level
+// i + 1), after both rows passes.  A CTA takes chunk offsets
 // [r0, r0 + RC) of one level-(i+1) window, whose column strip holds the rows
 // q'' < 4Q.  With zb' = IDFT_2Q(U_{i+1}) and zb_c = IDFT_Q(U_i of child c),
 // c1[q''] = conj(w_{2^(i+1)}^(r + C q'')) zb'[q''] and

@@ -26,7 +26,6 @@
 
 namespace mrdft {
 
-__device__ __forceinline__ int pad8(int a) { return a + (a >> 3); }
 template <int ZS>
 __device__ __forceinline__ int zlay(int a) {
   if constexpr (ZS >= 4) return a;
@@ -38,7 +37,6 @@ __device__ __forceinline__ int stg(int e) {
   if constexpr (B == 0) return e ^ ((e >> A) & 15);
   else return e ^ (((e >> A) ^ (e >> B)) & 15);
 }
-__host__ __device__ constexpr int pad8_size(int n) { return n + n / 8; }
 // two pad elements per 32 (level buffers: lane-consecutive 8-byte reads and
 // window-strided accesses stay conflict-free, and every pair (2k, 2k+1) stays
 // adjacent and 16-byte aligned, so a bin pair moves as one 16-byte access)

@@ -15,6 +15,7 @@
 //   k_fwd_cols / k_fwd_rows  one level i >= 15 in two passes: DFT_h with
 //                h = Q * C split as a length-Q DFT across C-sample chunks
 //                (cols) and a length-C DFT per output residue (rows).
+//   k_fwd_cols2  the cols passes of two consecutive levels from one read of x.
 #include <cuda_runtime.h>
 
 #include "mrdft_fft.cuh"
@@ -374,8 +375,8 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_fwd_cols(cons
   cg_fft<QB, QB, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
-// Two levels, one read of x: the cols passes of levels i and i + 1 (both with
-// C = 2^11, Q = 2^QB for level i and 2Q for level i + 1).  A CTA takes chunk
+// Two levels, one read of x: the cols passes of levels i and i + 1 (the same
+// C, Q = 2^QB for level i and 2Q for level i + 1).  A CTA takes chunk
 // offsets [r0, r0 + RC) of one level-(i+1) window, whose column strip holds the
 // rows q'' < 4Q; with x_j = x[r + C (q + j Q)] for j = 0..3,
 //   level i + 1 (halves a = rows < 2Q, b = the rest):

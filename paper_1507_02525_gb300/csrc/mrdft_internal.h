@@ -52,7 +52,7 @@ constexpr int kWinThreads = 256;             // levels 13, 14: 16 or 32 points p
 constexpr int kPassElemsLog = 13;
 constexpr int kPassThreads = 256;        // 2^13-point rows / adjoint cols CTAs
 constexpr int kColsThreads = 512;        // forward cols and 2^12-point adjoint rows CTAs (64 registers)
-constexpr int kPassThreadsWide = 512;    // the 2^14-point rows CTA (level 26)
+constexpr int kPassThreadsWide = 512;    // 2^14-point rows CTAs (levels 24 and 26)
 // rows CTA size: 2^13 points (2^14 for C = 2^14); for the adjoint's C <= 2^10
 // it gives the 2^12-point CTAs taken when AdjArgs.rows13 = 0 (2^13 otherwise)
 __host__ __device__ constexpr int rows_elems_log_c(int cb, bool adj) {
@@ -121,8 +121,8 @@ cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_adj_cols(const AdjArgs& a, int grid, cudaStream_t s);
 // cols passes of levels a.level - 1 and a.level after both rows passes, one
-// update of acc; grid = level-a.level items; needs cols_log(., adj) == 10 and
-// a.level - 12 in [4, 9]
+// update of acc; grid = level-a.level items; both levels with the same C,
+// Q of the lower in [2^4, 2^9]
 cudaError_t launch_adj_cols2(const AdjArgs& a, int grid, cudaStream_t s);
 bool adj_cols2_pairable(int upper_level, int cb_min);
 
