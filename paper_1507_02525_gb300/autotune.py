@@ -4,11 +4,11 @@ The transform's result does not depend on how a plan cuts its signals into
 segments (at most 2^seg_log samples each, whose level chains run concurrently
 on `streams` worker streams; see mrdft_plan_opts in include/mrdft.h), but its
 speed does: segments small enough for their levels to stay in L2 but large
-enough to fill the GPU.  `tune` times the forward (and, optionally, the
-adjoint) of every candidate shape on scratch buffers of the plan's own size,
-with CUDA events after warm-up, and keeps the fastest; results are cached per
-(device, dtype, batch, length list) in a JSON file so that a process plans
-tuned shapes without timing again.
+enough to fill the GPU.  `tune` times the forward, the adjoint or both (the
+objective) of every candidate shape on scratch buffers of the plan's own
+size, with CUDA events after warm-up, and keeps the fastest; results are
+cached per (device, dtype, batch, length list, objective) in a JSON file so
+that a process plans tuned shapes without timing again.
 
 The cache lives at $MRDFT_AUTOTUNE_CACHE, else
 ~/.cache/paper_1507_02525_gb300/autotune.json.  Cache handling is host-only
@@ -23,7 +23,8 @@ import threading
 from typing import Callable, Dict, Iterable, List, Optional, Sequence, Tuple
 
 DEFAULT_CANDIDATES: Tuple[Tuple[int, int], ...] = (
-    (20, 4), (21, 4), (22, 4), (23, 2), (23, 4), (24, 2), (26, 1))
+    (20, 4), (21, 2), (21, 4), (22, 2), (22, 4), (23, 2), (23, 4), (24, 2), (26, 1))
+OBJECTIVES = ("both", "forward", "adjoint")
 
 _lock = threading.Lock()
 
@@ -75,27 +76,36 @@ def pick(timings: Dict[Tuple[int, int], float]) -> Tuple[int, int]:
 
 def tune(lengths: Sequence[int], batch: Optional[int] = None, real_input: bool = False,
          candidates: Iterable[Tuple[int, int]] = DEFAULT_CANDIDATES, adjoint: bool = True,
-         reps: int = 5, use_cache: bool = True, timer: Optional[Callable] = None) -> Tuple[int, int]:
+         reps: int = 5, use_cache: bool = True, timer: Optional[Callable] = None,
+         objective: Optional[str] = None) -> Tuple[int, int]:
     """Best (seg_log, streams) for this plan configuration on the current GPU.
 
-    `timer(seg_log, streams) -> ms` may replace the GPU timing (tests)."""
+    `objective` is what is timed: "both" (forward + adjoint, the default),
+    "forward" or "adjoint" (a plan used in one direction only); `adjoint=False`
+    is the same as "forward".  `timer(seg_log, streams) -> ms` may replace the
+    GPU timing (tests)."""
+    objective = objective or ("both" if adjoint else "forward")
+    if objective not in OBJECTIVES:
+        raise ValueError(f"objective must be one of {OBJECTIVES}")
     lengths = [int(v) for v in lengths]
     batch = len(lengths) if batch is None else int(batch)
     import torch
     dev_name = torch.cuda.get_device_name() if timer is None else "test-device"
     key = cache_key(dev_name, real_input, batch, lengths if len(lengths) == batch else lengths * batch)
+    if objective != "both":
+        key += f"|{objective}"
     if use_cache:
         hit = load_cache().get(key)
         if hit and "seg_log" in hit and "streams" in hit:
             return int(hit["seg_log"]), int(hit["streams"])
     if timer is None:
-        timer = _gpu_timer(lengths, batch, real_input, adjoint, reps)
-    maxlog = max(int(v).bit_length() - 1 for v in lengths)
+        timer = _gpu_timer(lengths, batch, real_input, objective, reps)
+    total = sum(lengths) if len(lengths) == batch else sum(lengths) * batch
     cands: List[Tuple[int, int]] = []
     for s, k in candidates:
         s = min(max(int(s), 12), 26)
-        if s > maxlog and any(c[0] > maxlog for c in cands):
-            continue  # every segment size above the longest signal is the same plan
+        if (1 << s) >= total and any((1 << c[0]) >= total for c in cands):
+            continue  # once one segment holds every signal, larger segments give the same plan
         if (s, k) not in cands:
             cands.append((s, int(k)))
     timings = {c: float(timer(*c)) for c in cands}
@@ -106,7 +116,7 @@ def tune(lengths: Sequence[int], batch: Optional[int] = None, real_input: bool =
     return best
 
 
-def _gpu_timer(lengths, batch, real_input, adjoint, reps):
+def _gpu_timer(lengths, batch, real_input, objective, reps):
     import torch
     from . import _lib
 
@@ -122,9 +132,11 @@ def _gpu_timer(lengths, batch, real_input, adjoint, reps):
         plan = _lib.Plan(lengths, batch, real_input=real_input, graph=True, seg_log=seg_log, streams=streams)
         try:
             def step():
-                plan.forward(x.data_ptr(), y.data_ptr(), sp)
-                if adjoint:
+                if objective != "adjoint":
+                    plan.forward(x.data_ptr(), y.data_ptr(), sp)
+                if objective != "forward":
                     plan.adjoint(y.data_ptr(), gx.data_ptr(), sp)
+            plan.forward(x.data_ptr(), y.data_ptr(), sp)  # the adjoint's input: a real spectrum
             for _ in range(2):
                 step()
             torch.cuda.synchronize()

@@ -47,8 +47,18 @@ def test_tune_drops_equivalent_large_segments(tmp_path, monkeypatch):
     seen = []
     autotune.tune([1 << 16] * 4, 4, timer=lambda s, k: seen.append((s, k)) or 1.0,
                   candidates=[(20, 4), (22, 4), (23, 2), (16, 2)])
-    # signals of 2^16: segments of 2^20, 2^22, 2^23 are all "whole signals"
+    # 4 signals of 2^16 (2^18 samples): segments of 2^20, 2^22, 2^23 all hold the whole batch
     assert (16, 2) in seen and sum(1 for s, _ in seen if s > 16) == 1
+
+
+def test_tune_keeps_segment_sizes_that_group_signals(tmp_path, monkeypatch):
+    monkeypatch.setenv("MRDFT_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    seen = []
+    autotune.tune([1 << 16], 256, timer=lambda s, k: seen.append((s, k)) or 1.0,
+                  candidates=[(20, 4), (22, 4), (23, 2), (24, 2), (26, 1)])
+    # 256 signals of 2^16 (2^24 samples): 2^20, 2^22, 2^23 group 16, 64, 128 signals per
+    # segment; 2^24 and 2^26 both hold the whole batch
+    assert seen == [(20, 4), (22, 4), (23, 2), (24, 2)]
 
 
 def test_corrupt_cache_is_ignored(tmp_path, monkeypatch):
@@ -57,3 +67,18 @@ def test_corrupt_cache_is_ignored(tmp_path, monkeypatch):
     monkeypatch.setenv("MRDFT_AUTOTUNE_CACHE", str(p))
     assert autotune.load_cache() == {}
     assert autotune.tune([256], 1, timer=lambda s, k: float(s), candidates=[(12, 1), (13, 2)]) in [(12, 1), (13, 2)]
+
+
+def test_objective_is_part_of_the_key(tmp_path, monkeypatch):
+    monkeypatch.setenv("MRDFT_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    fwd = autotune.tune([1 << 24], 1, timer=lambda s, k: abs(s - 22) + 0.1 * k, objective="forward",
+                        candidates=[(22, 2), (23, 2)])
+    adj = autotune.tune([1 << 24], 1, timer=lambda s, k: abs(s - 23) + 0.1 * k, objective="adjoint",
+                        candidates=[(22, 2), (23, 2)])
+    both = autotune.tune([1 << 24], 1, timer=lambda s, k: float(k), candidates=[(22, 4), (23, 2)])
+    assert (fwd, adj, both) == ((22, 2), (23, 2), (23, 2))
+    assert len(json.loads((tmp_path / "tune.json").read_text())) == 3
+    # adjoint=False is the forward objective, served from the cache
+    assert autotune.tune([1 << 24], 1, timer=lambda s, k: 1 / 0, adjoint=False) == (22, 2)
+    with pytest.raises(ValueError):
+        autotune.tune([1 << 24], 1, timer=lambda s, k: 1.0, objective="sideways")
