@@ -315,7 +315,8 @@ def test_maximum_length_2_26(oracle):
     y = y.view(26, N)
     x128 = x.astype(np.complex128)
     xn = float(np.linalg.norm(x128))
-    for i, pos in [(1, 5), (5, N - 1), (12, 123456), (16, 7_000_001), (21, 3), (26, 0), (26, N // 2 + 1)]:
+    for i, pos in [(1, 5), (5, N - 1), (12, 123456), (16, 7_000_001), (21, 3), (23, 40_000_001),
+                   (24, N - 3), (25, 12_345_679), (25, (1 << 25) + 7), (26, 0), (26, N // 2 + 1)]:
         ref = oracle.bin_value(x128, i, pos)
         assert abs(complex(y[i - 1, pos].item()) - ref) <= 1e-5 * xn, f"level {i} pos {pos}"
     del y, xt
@@ -443,6 +444,37 @@ def test_adjoint_dot_product_16m():
         rhs = torch.vdot(gx.to(torch.complex128), x.to(torch.complex128)).item()
         assert abs(lhs - rhs) <= 1e-5 * abs(lhs), (lhs, rhs)
     del x, g, y, gx
+    torch.cuda.empty_cache()
+
+
+def test_adjoint_dot_product_64m():
+    """<M x, g> = <x, M^H g> at the maximum length N = 2^26 (top levels 24-26,
+    C = 2^12..2^14), sums in FP64 on the GPU."""
+    N = 1 << 26
+    plan = _lib.Plan([N], 1)
+    gen = torch.Generator(device="cuda").manual_seed(26)
+    x = torch.randn(N, dtype=torch.complex64, device="cuda", generator=gen)
+    g = torch.randn(plan.out_elems, dtype=torch.complex64, device="cuda", generator=gen)
+    y = torch.empty(plan.out_elems, dtype=torch.complex64, device="cuda")
+    gx = torch.empty(N, dtype=torch.complex64, device="cuda")
+    sp = torch.cuda.current_stream().cuda_stream
+    plan.forward(x.data_ptr(), y.data_ptr(), sp)
+    plan.adjoint(g.data_ptr(), gx.data_ptr(), sp)
+    torch.cuda.synchronize()
+    plan.status_poll()
+    lhs = sum(torch.vdot(g[o:o + N].to(torch.complex128), y[o:o + N].to(torch.complex128)).item()
+              for o in range(0, plan.out_elems, N))
+    rhs = torch.vdot(gx.to(torch.complex128), x.to(torch.complex128)).item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs), (lhs, rhs)
+    # the top level alone: the adjoint of level 26 is an unnormalised inverse DFT of the whole signal
+    g.zero_()
+    g[25 * N:26 * N] = torch.randn(N, dtype=torch.complex64, device="cuda", generator=gen)
+    plan.adjoint(g.data_ptr(), gx.data_ptr(), sp)
+    torch.cuda.synchronize()
+    ref = torch.fft.ifft(g[25 * N:26 * N].to(torch.complex128)) * N
+    err = (torch.linalg.vector_norm(gx.to(torch.complex128) - ref) / torch.linalg.vector_norm(ref)).item()
+    assert err <= 1e-5, err
+    del x, g, y, gx, ref
     torch.cuda.empty_cache()
 
 
