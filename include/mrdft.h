@@ -27,8 +27,8 @@
  *
  * Errors: every call returns an mrdft_status; nothing throws across the ABI.
  * A failed call leaves a message retrievable with mrdft_last_error().
- * Kernels report asynchronous faults (a wait that gave up, an invalid work
- * item) in a device status word read back by mrdft_status_poll().
+ * Kernels report an invalid work item in a device status word read back by
+ * mrdft_status_poll() (no kernel waits on a flag or on another kernel).
  */
 #ifndef MRDFT_H_
 #define MRDFT_H_
@@ -48,7 +48,7 @@ typedef enum {
   MRDFT_ENOMEM = 2,       /* device or host allocation failed */
   MRDFT_ECUDA = 3,        /* a CUDA runtime call failed (message in mrdft_last_error) */
   MRDFT_EUNSUPPORTED = 4, /* valid request the library does not implement */
-  MRDFT_ETIMEOUT = 5,     /* a device-side wait gave up (reported by mrdft_status_poll) */
+  MRDFT_ETIMEOUT = 5,     /* a device-side wait gave up (reserved: no kernel waits on a flag) */
   MRDFT_EDEVICE = 6       /* a kernel flagged an invalid work item (mrdft_status_poll) */
 } mrdft_status;
 
