@@ -27,8 +27,11 @@
  *
  * Errors: every call returns an mrdft_status; nothing throws across the ABI.
  * A failed call leaves a message retrievable with mrdft_last_error().
- * Kernels report an invalid work item in a device status word read back by
- * mrdft_status_poll() (no kernel waits on a flag or on another kernel).
+ * Every kernel checks each work item it is given against the plan's signal
+ * descriptors before touching memory; an item that does not describe part of
+ * a planned signal (a work list damaged in device memory) is skipped and
+ * raises MRDFT_EDEVICE in a device status word that mrdft_status_poll()
+ * reads back.  No kernel waits on a flag or on another kernel.
  */
 #ifndef MRDFT_H_
 #define MRDFT_H_
@@ -75,13 +78,10 @@ typedef enum {
  *   flags     : MRDFT_FLAG_* bits.
  * Returns MRDFT_EINVAL for a bad length or count, MRDFT_ENOMEM / MRDFT_ECUDA
  * when allocation fails.  The plan is bound to the device current at the
- * call; it may be used from one stream at a time.
- * Environment variables read here change only the speed, never the result:
- * MRDFT_SEG_LOG, MRDFT_STREAMS (execution shape, see mrdft_plan_opts),
- * MRDFT_DUAL_COLS=0 (one cols pass per two-pass level instead of one per
- * pair), MRDFT_FWD_CB / MRDFT_ADJ_CB (two-pass split C = 2^max(i-12, cb);
- * defaults 9 and 10), MRDFT_FWD_ROWS14=0 and MRDFT_ADJ_ROWS13=0 (smaller
- * rows CTAs for the C = 2^12 forward and C <= 2^10 adjoint levels).
+ * call; it may be used from one stream at a time.  The execution shape and
+ * kernel variants take the library defaults (see mrdft_plan_ex); the
+ * environment variables MRDFT_SEG_LOG and MRDFT_STREAMS override the default
+ * segment size and stream count (speed only, never the result).
  */
 mrdft_status mrdft_plan(mrdft_plan_t* out, const int64_t* lengths, int64_t n_lengths,
                         int64_t batch, int dtype, uint32_t flags);
@@ -98,6 +98,51 @@ mrdft_status mrdft_plan(mrdft_plan_t* out, const int64_t* lengths, int64_t n_len
  */
 mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t n_lengths, int64_t batch,
                              int dtype, uint32_t flags, int32_t seg_log, int32_t streams);
+
+/*
+ * Execution options of a plan.  None of them changes the result (every
+ * variant computes Eq. 1 with the same recursion, only the launch shapes
+ * differ); they change the speed, and the autotuner of the Python package
+ * times candidates through mrdft_plan_ex.  A field left at 0 takes the
+ * library default; switches take MRDFT_OPT_OFF or MRDFT_OPT_ON.
+ *   seg_log  : segments of at most 2^seg_log samples, 12..26 (default 23)
+ *   streams  : worker streams the segment chains run on, 1..16 (default 4)
+ *   fwd_cb   : forward two-pass split h = Q C, C = 2^max(i - 12, fwd_cb), 9..11 (default 9)
+ *   adj_cb   : adjoint two-pass split, 9..10 (default 10)
+ *   fwd_rows_prefetch : forward rows CTAs copy the children spectra into
+ *              shared memory when they start (default on)
+ *   fwd_rows14 : with prefetch off, C = 2^12 forward rows CTAs of 2^14
+ *              points instead of 2^13 (default on)
+ *   adj_rows13 : adjoint C = 2^10 rows CTAs of 2^13 points instead of 2^12 (default on)
+ *   dual_cols : consecutive two-pass levels of a chain share one cols pass (default on)
+ *   fwd_tree : the forward runs each window of a level above the segment
+ *              size as soon as its two children are done (default on);
+ *              off: those levels run level by level after every segment
+ */
+#define MRDFT_OPT_DEFAULT 0
+#define MRDFT_OPT_OFF 1
+#define MRDFT_OPT_ON 2
+typedef struct {
+  int32_t seg_log;
+  int32_t streams;
+  int32_t fwd_cb;
+  int32_t adj_cb;
+  int32_t fwd_rows_prefetch;
+  int32_t fwd_rows14;
+  int32_t adj_rows13;
+  int32_t dual_cols;
+  int32_t fwd_tree;
+} mrdft_exec_opts;
+
+/*
+ * mrdft_plan_ex -- mrdft_plan with execution options (NULL: all defaults).
+ * MRDFT_EINVAL for a field out of its range, otherwise as mrdft_plan.
+ */
+mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_lengths, int64_t batch,
+                           int dtype, uint32_t flags, const mrdft_exec_opts* opts);
+
+/* The execution options a plan runs with (every field filled in). */
+mrdft_status mrdft_plan_get_opts(mrdft_plan_t plan, mrdft_exec_opts* opts);
 
 /* Total complex outputs of the plan, sum_s m_s N_s (the length of y and gy). */
 mrdft_status mrdft_output_elems(mrdft_plan_t plan, int64_t* elems);
@@ -132,7 +177,11 @@ mrdft_status mrdft_adjoint(mrdft_plan_t plan, const void* gy, void* gx, mrdft_st
 mrdft_status mrdft_forward_host(mrdft_plan_t plan, const void* x_host, void* y_host,
                                 mrdft_stream_t stream);
 
-/* Read and clear the device status word; waits for the plan's last work. */
+/* Read and clear the plan's device status word; waits for the device.
+ * Returns MRDFT_EDEVICE when a kernel skipped an invalid work item since the
+ * last poll.  plan == NULL polls the status word of mrdft_forward_noalloc on
+ * the current device instead (MRDFT_OK if that entry point has not run on
+ * it; its error message is then read with mrdft_last_error(NULL)). */
 mrdft_status mrdft_status_poll(mrdft_plan_t plan);
 
 /* Message of the last failed call on this plan (or of the last failed
@@ -215,6 +264,29 @@ mrdft_status mrdft_loss_grad(mrdft_plan_t plan, const void* x, const void* t, vo
  */
 #define MRDFT_NOALLOC_MAX_LOG 16
 mrdft_status mrdft_forward_noalloc(const void* x, void* y, int64_t n, mrdft_stream_t stream);
+
+/*
+ * mrdft_plan_graph_stats -- graph replay bookkeeping of a MRDFT_FLAG_GRAPH
+ * plan: `cached` executable graphs held (at most 4 per direction; a new
+ * (buffers, stream) combination past that re-targets the least recently
+ * used one with cudaGraphExecUpdate), `captures` stream captures made and
+ * `updates` of them that re-targeted an existing graph instead of
+ * instantiating a new one.  Any output pointer may be NULL.
+ */
+mrdft_status mrdft_plan_graph_stats(mrdft_plan_t plan, int32_t* cached, int64_t* captures, int64_t* updates);
+
+/*
+ * mrdft_debug_item -- test hook of the device-side work-item checks: reads
+ * (old_fields, may be NULL) and optionally overwrites (new_fields, may be
+ * NULL) work item `index` of the plan's tile list (list 0) or level list
+ * (list 1), four 32-bit words each, synchronously.  Level items are
+ * {signal, window, block, 0}; tile items {signal-list offset,
+ * count | (log2 tile length << 16), tile index, 0}.  MRDFT_EINVAL for an
+ * index past the end of the list.  A kernel given an item that does not fit
+ * its signal skips it and mrdft_status_poll() then returns MRDFT_EDEVICE.
+ */
+mrdft_status mrdft_debug_item(mrdft_plan_t plan, int list, int64_t index, const int32_t* new_fields,
+                              int32_t* old_fields);
 
 /* Release everything the plan owns.  NULL is ignored. */
 void mrdft_destroy(mrdft_plan_t plan);

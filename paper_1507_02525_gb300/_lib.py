@@ -28,14 +28,42 @@ STATUS_NAMES = {0: "MRDFT_OK", 1: "MRDFT_EINVAL", 2: "MRDFT_ENOMEM", 3: "MRDFT_E
                 4: "MRDFT_EUNSUPPORTED", 5: "MRDFT_ETIMEOUT", 6: "MRDFT_EDEVICE"}
 
 # every entry point declared in include/mrdft.h
-EXPORTS = ("mrdft_plan", "mrdft_plan_opts", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
+EXPORTS = ("mrdft_plan", "mrdft_plan_opts", "mrdft_plan_ex", "mrdft_plan_get_opts", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
            "mrdft_adjoint", "mrdft_forward_host", "mrdft_status_poll", "mrdft_last_error",
            "mrdft_plan_info", "mrdft_timing_enable", "mrdft_timing_read", "mrdft_loss_grad",
-           "mrdft_forward_noalloc", "mrdft_destroy")
+           "mrdft_forward_noalloc", "mrdft_plan_graph_stats", "mrdft_debug_item", "mrdft_destroy")
 NOALLOC_MAX_LOG = 16
 
 KINDS = ("fwd_tile", "fwd_tiny", "fwd_window", "fwd_cols", "fwd_rows",
          "adj_tile", "adj_tiny", "adj_window", "adj_rows", "adj_cols")
+
+
+OPT_DEFAULT, OPT_OFF, OPT_ON = 0, 1, 2
+
+
+class ExecOpts(ctypes.Structure):
+    """mrdft_exec_opts (include/mrdft.h): 0 = library default; switches 1 = off, 2 = on."""
+    _fields_ = [(n, ctypes.c_int32) for n in ("seg_log", "streams", "fwd_cb", "adj_cb", "fwd_rows_prefetch",
+                                               "fwd_rows14", "adj_rows13", "dual_cols", "fwd_tree")]
+    SWITCHES = ("fwd_rows_prefetch", "fwd_rows14", "adj_rows13", "dual_cols", "fwd_tree")
+
+    @classmethod
+    def from_dict(cls, d):
+        """Fields by name; switches may be given as bools."""
+        o = cls()
+        for k, v in (d or {}).items():
+            if k not in dict(cls._fields_):
+                raise ValueError(f"unknown execution option {k!r}")
+            if k in cls.SWITCHES and isinstance(v, bool):
+                v = OPT_ON if v else OPT_OFF
+            setattr(o, k, int(v or 0))
+        return o
+
+    def to_dict(self):
+        d = {n: getattr(self, n) for n, _ in self._fields_}
+        for k in self.SWITCHES:
+            d[k] = {OPT_ON: True, OPT_OFF: False}.get(d[k], None)
+        return d
 
 
 class MrdftError(RuntimeError):
@@ -65,6 +93,9 @@ def load(build_if_missing: bool = True):
         vp, i64, i32, u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32
         lib.mrdft_plan.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), i64, i64, i32, u32]
         lib.mrdft_plan_opts.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), i64, i64, i32, u32, i32, i32]
+        lib.mrdft_plan_ex.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(i64), i64, i64, i32, u32,
+                                      ctypes.POINTER(ExecOpts)]
+        lib.mrdft_plan_get_opts.argtypes = [vp, ctypes.POINTER(ExecOpts)]
         lib.mrdft_output_elems.argtypes = [vp, ctypes.POINTER(i64)]
         lib.mrdft_input_elems.argtypes = [vp, ctypes.POINTER(i64)]
         lib.mrdft_forward.argtypes = [vp, vp, vp, vp]
@@ -81,11 +112,16 @@ def load(build_if_missing: bool = True):
         lib.mrdft_loss_grad.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         lib.mrdft_forward_noalloc.argtypes = [vp, vp, i64, vp]
         lib.mrdft_forward_noalloc.restype = ctypes.c_int
+        lib.mrdft_plan_graph_stats.argtypes = [vp, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(i64),
+                                               ctypes.POINTER(i64)]
+        lib.mrdft_debug_item.argtypes = [vp, i32, i64, ctypes.POINTER(ctypes.c_int32),
+                                         ctypes.POINTER(ctypes.c_int32)]
         lib.mrdft_destroy.argtypes = [vp]
         lib.mrdft_destroy.restype = None
-        for name in ("mrdft_plan", "mrdft_plan_opts", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
+        for name in ("mrdft_plan", "mrdft_plan_opts", "mrdft_plan_ex", "mrdft_plan_get_opts", "mrdft_output_elems", "mrdft_input_elems", "mrdft_forward",
                      "mrdft_adjoint", "mrdft_forward_host", "mrdft_status_poll", "mrdft_plan_info",
-                     "mrdft_timing_enable", "mrdft_timing_read", "mrdft_loss_grad"):
+                     "mrdft_timing_enable", "mrdft_timing_read", "mrdft_loss_grad", "mrdft_plan_graph_stats",
+                     "mrdft_debug_item"):
             getattr(lib, name).restype = ctypes.c_int
         _lib = lib
         return lib
@@ -108,16 +144,25 @@ class Plan:
     """Owner of an ``mrdft_plan_t`` (see ``mrdft_plan`` in include/mrdft.h)."""
 
     def __init__(self, lengths, batch: int | None = None, real_input: bool = False,
-                 graph: bool = False, seg_log: int | None = None, streams: int | None = None):
+                 graph: bool = False, seg_log: int | None = None, streams: int | None = None,
+                 opts: dict | None = None):
+        """``opts``: execution options by name (mrdft_exec_opts); ``seg_log`` and
+        ``streams`` are shorthands for two of them."""
         lib = load()
         lengths = [int(v) for v in (lengths if hasattr(lengths, "__len__") else [lengths])]
         if batch is None:
             batch = len(lengths)
         arr = (ctypes.c_int64 * len(lengths))(*lengths)
         h = ctypes.c_void_p()
-        st = lib.mrdft_plan_opts(ctypes.byref(h), arr, len(lengths), int(batch),
-                                 MRDFT_R32 if real_input else MRDFT_C64,
-                                 MRDFT_FLAG_GRAPH if graph else 0, int(seg_log or 0), int(streams or 0))
+        o = dict(opts or {})
+        if seg_log:
+            o["seg_log"] = seg_log
+        if streams:
+            o["streams"] = streams
+        eo = ExecOpts.from_dict(o)
+        st = lib.mrdft_plan_ex(ctypes.byref(h), arr, len(lengths), int(batch),
+                               MRDFT_R32 if real_input else MRDFT_C64,
+                               MRDFT_FLAG_GRAPH if graph else 0, ctypes.byref(eo))
         check(st, None)
         self._h = h
         self._lib = lib
@@ -136,6 +181,12 @@ class Plan:
     @property
     def handle(self):
         return self._h
+
+    def opts(self) -> dict:
+        """The execution options the plan runs with."""
+        eo = ExecOpts()
+        check(self._lib.mrdft_plan_get_opts(self._h, ctypes.byref(eo)), self._h)
+        return eo.to_dict()
 
     def info(self):
         a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
@@ -180,6 +231,23 @@ class Plan:
 
     def status_poll(self) -> None:
         check(self._lib.mrdft_status_poll(self._h), self._h)
+
+    def graph_stats(self) -> dict:
+        """Executable graphs held, captures made, captures that re-targeted a held graph."""
+        c, n, u = ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+        check(self._lib.mrdft_plan_graph_stats(self._h, ctypes.byref(c), ctypes.byref(n), ctypes.byref(u)), self._h)
+        return {"cached": c.value, "captures": n.value, "updates": u.value}
+
+    def debug_item(self, lst: int, index: int, new=None):
+        """Read (and with ``new`` overwrite) work item ``index`` of list 0 (tiles)
+        or 1 (levels) as four int32 words; None past the end of the list."""
+        old = (ctypes.c_int32 * 4)()
+        nw = (ctypes.c_int32 * 4)(*new) if new is not None else None
+        st = self._lib.mrdft_debug_item(self._h, int(lst), int(index), nw, old)
+        if st == MRDFT_EINVAL:
+            return None
+        check(st, self._h)
+        return list(old)
 
     def close(self) -> None:
         if getattr(self, "_h", None):

@@ -23,7 +23,7 @@ def get_plan(lengths, batch: int, real_input: bool, graph: bool = False, device=
              tune: bool = False) -> _lib.Plan:
     """Plan for the given signal lengths (cached per device and configuration).
 
-    With tune=True the execution shape comes from the autotuner (timed once
+    With tune=True the execution options come from the autotuner (timed once
     per configuration and device, then read from its JSON cache)."""
     dev = torch.cuda.current_device() if device is None else torch.device(device).index
     key = (tuple(int(v) for v in lengths), int(batch), bool(real_input), bool(graph), dev, bool(tune))
@@ -31,12 +31,11 @@ def get_plan(lengths, batch: int, real_input: bool, graph: bool = False, device=
         p = _plans.get(key)
         if p is None:
             with torch.cuda.device(dev):
-                seg_log = streams = None
+                opts = {}
                 if tune:
                     from . import autotune
-                    seg_log, streams = autotune.tune(list(key[0]), batch, real_input)
-                p = _lib.Plan(list(key[0]), batch=batch, real_input=real_input, graph=graph,
-                              seg_log=seg_log, streams=streams)
+                    opts = autotune.tune_plan(list(key[0]), batch, real_input, objective="both")
+                p = _lib.Plan(list(key[0]), batch=batch, real_input=real_input, graph=graph, opts=opts)
             _plans[key] = p
         return p
 

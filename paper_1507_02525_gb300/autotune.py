@@ -1,14 +1,19 @@
-"""Autotuner of a plan's execution shape, with a JSON cache.
+"""Autotuner of a plan's execution options, with a JSON cache.
 
 The transform's result does not depend on how a plan cuts its signals into
 segments (at most 2^seg_log samples each, whose level chains run concurrently
-on `streams` worker streams; see mrdft_plan_opts in include/mrdft.h), but its
-speed does: segments small enough for their levels to stay in L2 but large
-enough to fill the GPU.  `tune` times the forward, the adjoint or both (the
-objective) of every candidate shape on scratch buffers of the plan's own
-size, with CUDA events after warm-up, and keeps the fastest; results are
+on `streams` worker streams), nor on the kernel variants it launches (the
+two-pass split C of the large levels, the rows CTA shape, the pairing of two
+levels in one cols pass, the tree schedule of the levels above a segment; see
+mrdft_exec_opts in include/mrdft.h), but its speed does.  `tune_plan` times
+the forward, the adjoint or both (the objective) on scratch buffers of the
+plan's own size, with CUDA events after warm-up: first every candidate shape
+with the default kernel variants, then each kernel variant in turn on the
+best shape (coordinate descent: a variant is kept only when it is faster by
+more than 1%), and returns the options of the fastest plan.  Results are
 cached per (device, dtype, batch, length list, objective) in a JSON file so
-that a process plans tuned shapes without timing again.
+that a process plans tuned options without timing again.  `tune` is the
+shape-only search.
 
 The cache lives at $MRDFT_AUTOTUNE_CACHE, else
 ~/.cache/paper_1507_02525_gb300/autotune.json.  Cache handling is host-only
@@ -25,6 +30,26 @@ from typing import Callable, Dict, Iterable, List, Optional, Sequence, Tuple
 DEFAULT_CANDIDATES: Tuple[Tuple[int, int], ...] = (
     (20, 4), (21, 2), (21, 4), (22, 2), (22, 4), (23, 2), (23, 4), (24, 2), (26, 1))
 OBJECTIVES = ("both", "forward", "adjoint")
+
+# kernel variants searched after the shape, per objective: (option, values);
+# the first value of each is the library default
+FWD_KNOBS = (("fwd_cb", (9, 10, 11)), ("fwd_rows_prefetch", (True, False)), ("dual_cols", (True, False)),
+             ("fwd_tree", (True, False)))
+ADJ_KNOBS = (("adj_cb", (10, 9)), ("adj_rows13", (True, False)), ("dual_cols", (True, False)))
+KEEP_MARGIN = 0.99  # a variant replaces the current choice only when at least 1% faster
+
+
+def knobs_for(objective: str, lengths: Sequence[int], seg_log: int):
+    """The kernel variants that can change this workload's plan: the two-pass
+    ones only when some signal has two-pass levels (N > 2^14), the tree only
+    when some signal is longer than a segment."""
+    mx = max(int(v) for v in lengths)
+    if mx <= (1 << 14):
+        return ()
+    knobs = {"forward": FWD_KNOBS, "adjoint": ADJ_KNOBS}.get(objective)
+    if knobs is None:  # both: the union, in order
+        knobs = FWD_KNOBS + tuple(k for k in ADJ_KNOBS if k[0] not in dict(FWD_KNOBS))
+    return tuple(k for k in knobs if k[0] != "fwd_tree" or mx > (1 << seg_log))
 
 _lock = threading.Lock()
 
@@ -116,6 +141,50 @@ def tune(lengths: Sequence[int], batch: Optional[int] = None, real_input: bool =
     return best
 
 
+def tune_plan(lengths: Sequence[int], batch: Optional[int] = None, real_input: bool = False,
+              objective: str = "both", candidates: Iterable[Tuple[int, int]] = DEFAULT_CANDIDATES,
+              reps: int = 5, use_cache: bool = True, timer: Optional[Callable] = None) -> dict:
+    """Execution options (a dict for ``_lib.Plan(opts=...)``) of the fastest plan
+    found for this configuration on the current GPU.  `timer(opts) -> ms` may
+    replace the GPU timing (tests)."""
+    if objective not in OBJECTIVES:
+        raise ValueError(f"objective must be one of {OBJECTIVES}")
+    lengths = [int(v) for v in lengths]
+    batch = len(lengths) if batch is None else int(batch)
+    full = lengths if len(lengths) == batch else lengths * batch
+    import torch
+    dev_name = torch.cuda.get_device_name() if timer is None else "test-device"
+    key = cache_key(dev_name, real_input, batch, full) + f"|{objective}|opts"
+    if use_cache:
+        hit = load_cache().get(key)
+        if hit and isinstance(hit.get("opts"), dict):
+            return dict(hit["opts"])
+    if timer is None:
+        gpu = _gpu_timer(lengths, batch, real_input, objective, reps)
+        timer = lambda o: gpu(o.get("seg_log"), o.get("streams"), o)  # noqa: E731
+    log = {}
+
+    def t(o):
+        k = json.dumps(o, sort_keys=True)
+        if k not in log:
+            log[k] = float(timer(dict(o)))
+        return log[k]
+
+    shape = tune(lengths, batch, real_input, candidates=candidates, use_cache=False, objective=objective,
+                 timer=lambda s_, k_: t({"seg_log": s_, "streams": k_}))
+    best = {"seg_log": shape[0], "streams": shape[1]}
+    best_ms = t(best)
+    for name, values in knobs_for(objective, full, shape[0]):
+        for v in values[1:]:
+            trial = dict(best, **{name: v})
+            ms = t(trial)
+            if ms < KEEP_MARGIN * best_ms:
+                best, best_ms = trial, ms
+    if use_cache:
+        store(key, {"opts": best, "ms": round(best_ms, 5), "timed": {k: round(v, 5) for k, v in log.items()}})
+    return best
+
+
 def _gpu_timer(lengths, batch, real_input, objective, reps):
     import torch
     from . import _lib
@@ -128,8 +197,9 @@ def _gpu_timer(lengths, batch, real_input, objective, reps):
     stream = torch.cuda.current_stream()
     sp = stream.cuda_stream
 
-    def timer(seg_log: int, streams: int) -> float:
-        plan = _lib.Plan(lengths, batch, real_input=real_input, graph=True, seg_log=seg_log, streams=streams)
+    def timer(seg_log: int, streams: int, opts: Optional[dict] = None) -> float:
+        plan = _lib.Plan(lengths, batch, real_input=real_input, graph=True, seg_log=seg_log, streams=streams,
+                         opts={k: v for k, v in (opts or {}).items() if k not in ("seg_log", "streams")})
         try:
             def step():
                 if objective != "adjoint":

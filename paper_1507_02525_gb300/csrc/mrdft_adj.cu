@@ -139,20 +139,35 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
   const int item = blockIdx.x;
   if (item >= a.nitems) return;
   const TileItem it = reinterpret_cast<const TileItem*>(a.items)[item];
+  if (!tile_item_head_ok(it, a.nids, TLOG)) {
+    if (tid == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
   const int tl = it.tlog;
   const int Tn = it.nsig << tl;
   const int tn_log = 31 - __clz(Tn);
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  __syncthreads();
   if (tid < it.nsig) {
-    const SigDesc sd = a.sigs[a.sig_ids[it.sig_list + tid]];
-    const int64_t t0 = (int64_t)it.tile << tl;
-    TS[tid] = AdjTileSig{sd.in_off + t0, sd.out_off + t0, sd.m, 0};
+    SigDesc sd;
+    if (tile_sig_ok(a.sigs, a.nsigs, a.sig_ids[it.sig_list + tid], it, sd)) {
+      const int64_t t0 = (int64_t)it.tile << tl;
+      TS[tid] = AdjTileSig{sd.in_off + t0, sd.out_off + t0, sd.m, 0};
+    } else {
+      bad = 1;
+    }
   }
   load_twq<NT>(TQ, TLOG, a.tw);
+  __syncthreads();
+  if (bad) {
+    if (tid == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
   // For a tile of a longer signal (one signal, m > tl) the large levels left
   // contributions in acc and the level-(tl+1) even-bin propagation in e_in.
   const SigDesc sd0 = a.sigs[a.sig_ids[it.sig_list]];
   const bool below = sd0.m > tl;
-  __syncthreads();
 #pragma unroll 4
   for (int c = tid; c < (Tn >> 1); c += NT) {
     const int e = c << 1;
@@ -249,7 +264,12 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
 // Signals with N <= 16: conjugate transpose of Eq. 1 term by term.
 template <bool FUSED>
 __global__ void k_adj_tiny(const AdjArgs a) {
-  const SigDesc sd = a.sigs[a.sig_ids[blockIdx.x]];
+  const int id = (int)blockIdx.x < a.nids ? a.sig_ids[blockIdx.x] : -1;
+  if (id < 0 || id >= a.nsigs || a.sigs[id].m < 1 || a.sigs[id].m > 4) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
+  const SigDesc sd = a.sigs[id];
   const int N = 1 << sd.m;
   const int n = threadIdx.x;
   float lsum = 0.f;
@@ -303,7 +323,11 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) 
   float2* TQ = sm + (1 << kWinMaxLog);          // quarter-wave w_{2^13}
   if ((int)blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
-  const SigDesc sd = a.sigs[it.sig];
+  SigDesc sd;
+  if (!level_item_ok(a.sigs, a.nsigs, it, i, 1, sd)) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
   const int64_t w = it.window;
   const bool add = sd.m > i;
   float2* acc = a.acc + 2 * sd.aux_off + (w << i);
@@ -402,7 +426,11 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
   }
   const int i = a.level;
   const int HB = i - 1, QB = HB - CB;
-  const SigDesc sd = a.sigs[it.sig];
+  SigDesc sd;
+  if (!level_item_ok(a.sigs, a.nsigs, it, i, pass_items(i), sd)) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
   const int64_t w = it.window;
   const int k0 = blk << KCB;
   // gradient pairs (2k, 2k+1): a batch of loads is issued before any store
@@ -467,7 +495,11 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_adj_cols(cons
   const int i = a.level;
   const int HB = i - 1, CB = HB - QB;
   const int64_t h = (int64_t)1 << HB;
-  const SigDesc sd = a.sigs[it.sig];
+  SigDesc sd;
+  if (!level_item_ok(a.sigs, a.nsigs, it, i, pass_items(i), sd)) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
   const int64_t w = it.window;
   const int r0 = ((it.block << SH) | ((int)blockIdx.x & ((1 << SH) - 1))) << RCB;
   const float2* U = a.scratch + sd.aux_off + (w << HB);
@@ -546,7 +578,11 @@ __global__ void __launch_bounds__(kColsThreads, 2) k_adj_cols2(const AdjArgs a) 
   if (item >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
   const int i1 = a.level, i = i1 - 1;                    // the pair (i, i + 1)
-  const SigDesc sd = a.sigs[it.sig];
+  SigDesc sd;
+  if (!level_item_ok(a.sigs, a.nsigs, it, i1, pass_items(i1), sd)) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
   const int64_t W = it.window;
   const int r0 = ((it.block << 1) | ((int)blockIdx.x & 1)) << RCB;
   const float2* U1 = a.scratch2 + sd.aux_off + (W << i);

@@ -130,15 +130,30 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
   const int item = blockIdx.x;
   if (item >= a.nitems) return;
   const TileItem it = reinterpret_cast<const TileItem*>(a.items)[item];
+  if (!tile_item_head_ok(it, a.nids, TLOG)) {
+    if (tid == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
   const int tl = it.tlog;
   const int Tn = it.nsig << tl;
   const int tn_log = 31 - __clz(Tn);
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  __syncthreads();
   if (tid < it.nsig) {
-    const SigDesc sd = a.sigs[a.sig_ids[it.sig_list + tid]];
-    const int64_t t0 = (int64_t)it.tile << tl;
-    TS[tid] = TileSig{sd.in_off + t0, sd.out_off + t0, sd.m, 0};
+    SigDesc sd;
+    if (tile_sig_ok(a.sigs, a.nsigs, a.sig_ids[it.sig_list + tid], it, sd)) {
+      const int64_t t0 = (int64_t)it.tile << tl;
+      TS[tid] = TileSig{sd.in_off + t0, sd.out_off + t0, sd.m, 0};
+    } else {
+      bad = 1;
+    }
   }
   __syncthreads();
+  if (bad) {
+    if (tid == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
   // ---- stage the tile of x (P^(1): x is read once and reused per level)
   if (!a.in_real) {
     const float2* xg = reinterpret_cast<const float2*>(a.x);
@@ -219,7 +234,12 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
 // Signals with N <= 16: Eq. 1 term by term, one thread per output bin.
 __global__ void k_fwd_tiny(const FwdArgs a) {
   const int s = blockIdx.x;
-  const SigDesc sd = a.sigs[a.sig_ids[s]];
+  const int id = s < a.nids ? a.sig_ids[s] : -1;
+  if (id < 0 || id >= a.nsigs || a.sigs[id].m < 1 || a.sigs[id].m > 4) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
+  const SigDesc sd = a.sigs[id];
   const int N = 1 << sd.m;
   const int t = threadIdx.x;  // output index over m * N
   if (t >= sd.m * N) return;
@@ -251,7 +271,11 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_fwd_window(const FwdArgs a) 
   float2* TQ = sm + (1 << kWinMaxLog);          // quarter-wave w_{2^13}
   if ((int)blockIdx.x >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
-  const SigDesc sd = a.sigs[it.sig];
+  SigDesc sd;
+  if (!level_item_ok(a.sigs, a.nsigs, it, i, 1, sd)) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
   const int64_t ws = (int64_t)it.window << i;
   const int64_t xs = sd.in_off + ws;
   const float2* yprev = a.y + sd.out_off + ((int64_t)(i - 2) << sd.m) + ws;
@@ -311,8 +335,12 @@ constexpr size_t cols_smem(int E) { return (size_t)((1 << E) + twq_size(12) + (1
 template <int QB>
 constexpr int cols_e() { return QB <= 10 ? 12 : kPassElemsLog; }
 // rows pass: work area, w_C table, twiddle tables KC (64 + 1) + KC (C / 64 + 16 / KC)
-constexpr size_t rows_smem(int E, int CB) {
-  return (size_t)((1 << E) + twq_size(CB) + (1 << (E - CB)) * 65 + (1 << (E - 6)) + 16) * sizeof(float2);
+// (PF: plus both children of every output bin, 2 x 2^E, from a 16-byte boundary)
+__host__ __device__ constexpr int rows_ch_off(int E, int CB) {
+  return ((1 << E) + twq_size(CB) + (1 << (E - CB)) * 65 + (1 << (E - 6)) + 16 + 1) & ~1;
+}
+constexpr size_t rows_smem(int E, int CB, bool PF = false) {
+  return (size_t)(rows_ch_off(E, CB) + (PF ? 2 << E : 0)) * sizeof(float2);
 }
 
 // =============================================================== two-pass
@@ -339,7 +367,11 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_fwd_cols(cons
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
   const int i = a.level;
   const int HB = i - 1, CB = HB - QB;
-  const SigDesc sd = a.sigs[it.sig];
+  SigDesc sd;
+  if (!level_item_ok(a.sigs, a.nsigs, it, i, pass_items(i), sd)) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
   const int64_t xs = sd.in_off + ((int64_t)it.window << i);
   const int r0 = ((it.block << SH) | ((int)blockIdx.x & ((1 << SH) - 1))) << RCB;
   const int64_t h = (int64_t)1 << HB;
@@ -405,7 +437,11 @@ __global__ void __launch_bounds__(kColsThreads, 2) k_fwd_cols2(const FwdArgs a) 
   if (item >= a.nitems) return;
   const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[item];
   const int i1 = a.level, i = i1 - 1;                    // the pair (i, i + 1)
-  const SigDesc sd = a.sigs[it.sig];
+  SigDesc sd;
+  if (!level_item_ok(a.sigs, a.nsigs, it, i1, pass_items(i1), sd)) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
   const int64_t xs = sd.in_off + ((int64_t)it.window << i1);
   const int r0 = ((it.block << 1) | ((int)blockIdx.x & 1)) << RCB;
   load_twq<NT>(TQ, 12, a.tw);
@@ -456,8 +492,12 @@ constexpr size_t cols2_smem() {
   return (size_t)((1 << kPassElemsLog) + twq_size(12) + 2 * (1 << (kPassElemsLog - 5))) * sizeof(float2);
 }
 
-template <int E, int NT, int CB>
-__global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : (E == kPassElemsLog ? 2 : 1)) k_fwd_rows(const FwdArgs a) {
+// PF: the children of every output bin are copied into shared memory
+// (cp.async) when the CTA starts, behind the intermediate, so that their
+// latency overlaps the whole FFT instead of stalling the last pass.
+template <int E, int NT, int CB, bool PF>
+__global__ void __launch_bounds__(NT, PF ? (E < kPassElemsLog ? 2 : 1) : (E < kPassElemsLog ? 4 : (E == kPassElemsLog ? 2 : 1)))
+    k_fwd_rows(const FwdArgs a) {
   constexpr int PTS = (1 << E) / NT;
   constexpr int C = 1 << CB;
   constexpr int KCB = E - CB, KC = 1 << KCB;
@@ -469,6 +509,8 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : (E == kPassElemsLo
   float2* TQ = sm + (1 << E);              // quarter-wave w_C
   float2* TWL = TQ + twq_size(CB);         // [KC][64] (row stride 65): w_h^(k2 t)
   float2* TWH = TWL + KC * 65;             // [KC][C/64] (row stride C/64 + 16/KC): w_h^(k2 64 u)
+  float2* CH = sm + rows_ch_off(E, CB);    // PF: child a of bin (k1, j) at k1 KC + j, child b 2^E further
+  static_assert(!PF || (KC >= 2 && (1 << E) / 8 >= NT), "children in 16-byte runs; every thread in the last pass");
   int item, blk;
   if constexpr (SH >= 0) {
     item = (int)blockIdx.x << SH;
@@ -485,7 +527,11 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : (E == kPassElemsLo
   const int i = a.level;
   const int HB = i - 1, QB = HB - CB;
   const int64_t h = (int64_t)1 << HB;
-  const SigDesc sd = a.sigs[it.sig];
+  SigDesc sd;
+  if (!level_item_ok(a.sigs, a.nsigs, it, i, pass_items(i), sd)) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
   const int64_t ws = (int64_t)it.window << i;
   const int k0 = blk << KCB;
   const float2* F = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
@@ -494,6 +540,17 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : (E == kPassElemsLo
   for (int e = threadIdx.x; e < KC * C; e += NT) {
     const int r = e & (C - 1), j = e >> CB;
     cp_async8(S + stg<SA, SB>((r << KCB) + j), F + ((int64_t)(k0 + j) << CB) + r);
+  }
+  if constexpr (PF) {
+    cp_async_commit();
+    // U (Eq. 2) inputs: bins k = k1 Q + k0 + j of both children, KC-bin runs
+#pragma unroll 8
+    for (int t = threadIdx.x; t < C * KC; t += NT) {
+      const int half = t >> (CB + KCB - 1), r = t & ((C * KC / 2) - 1);
+      const int k1 = r >> (KCB - 1), c = r & (KC / 2 - 1);
+      cp_async16(CH + (half << E) + (k1 << KCB) + 2 * c, yprev + half * h + ((int64_t)k1 << QB) + k0 + 2 * c);
+    }
+    cp_async_commit();
   }
   load_twq<NT>(TQ, CB, a.tw);
   for (int t = threadIdx.x; t < KC * (64 + HU); t += NT) {
@@ -505,7 +562,8 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : (E == kPassElemsLo
       TWH[j * (HU + 16 / KC) + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * 64 * u);
     }
   }
-  cp_async_wait_all();
+  if constexpr (PF) cp_async_wait<1>();  // the intermediate; the children may still be in flight
+  else cp_async_wait_all();
   __syncthreads();
   // the intermediate rows are dead now: drop them from L2 without write-back
   for (int l = threadIdx.x; l < KC * C / 16; l += NT) discard_l2(F + ((int64_t)k0 << CB) + 16 * l);
@@ -530,7 +588,19 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : (E == kPassElemsLo
     if (reread) __stcg(dst, v);
     else __stcs(dst, v);
   };
-  {
+  static_assert(3 * ((CB + 2) / 3 - 1) >= 6, "first-pass stride below 64");
+  if constexpr (PF) {
+    // the last pass waits for this thread's children copies before its
+    // barrier; after the barrier every thread's copies are visible
+    auto pre = [&](int slot, int, int) MRDFT_INL {
+      if (slot == 0) cp_async_wait<0>();
+    };
+    auto sink = [&](int, int b, int k1, float2 odd) MRDFT_INL {
+      const int e = (k1 << KCB) + b;
+      store(b, k1, cadd(CH[e], CH[(1 << E) + e]), odd);  // U (Eq. 2): child sum
+    };
+    cg_fft<CB, CB, NT, PTS, true, kPreBarrier, KCB, true>(S, CB, KCB, tw, src, pre, sink);
+  } else {
     float2 ea[PTS], eb[PTS];
     // U (Eq. 2): the children of bin k, read once per group of 8 bins
     auto pre = [&](int slot, int b, int k1) MRDFT_INL {
@@ -541,7 +611,6 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : (E == kPassElemsLo
     auto sink = [&](int slot, int b, int k1, float2 odd) MRDFT_INL {
       store(b, k1, cadd(ea[slot], eb[slot]), odd);
     };
-    static_assert(3 * ((CB + 2) / 3 - 1) >= 6, "first-pass stride below 64");
     cg_fft<CB, CB, NT, PTS, true, kPreHalf, KCB, true>(S, CB, KCB, tw, src, pre, sink);
   }
 }
@@ -555,17 +624,31 @@ void cols_launch(const FwdArgs& a, int grid, cudaStream_t s) {
 }
 template <int CB>
 constexpr int rows_e() { return rows_elems_log_c(CB, false); }
-template <int CB, int E = rows_e<CB>()>
+template <int E, bool PF>
+constexpr int rows_nt() {
+  return PF ? kColsThreads : (E < kPassElemsLog ? kPassThreads : (E == kPassElemsLog ? kColsThreads : kPassThreadsWide));
+}
+// children-prefetching rows CTAs: 2^12 points (8 residues, 2 CTAs per SM) at
+// C = 2^9, 2^13 points (one CTA per SM) above
+template <int CB>
+constexpr int rows_pf_e() { return CB <= 9 ? 12 : kPassElemsLog; }
+template <int CB, int E = rows_e<CB>(), bool PF = false>
 void rows_launch_e(const FwdArgs& a, int grid, cudaStream_t s) {
-  constexpr int NT = E < kPassElemsLog ? kPassThreads : (E == kPassElemsLog ? kColsThreads : kPassThreadsWide);
+  constexpr int NT = rows_nt<E, PF>();
   // a CTA of 2^E points takes 2^(E-13) items (E >= 13) or half an item
   int g;
   if constexpr (E >= kPassElemsLog) g = grid >> (E - kPassElemsLog);
   else g = grid << (kPassElemsLog - E);
-  k_fwd_rows<E, NT, CB><<<g, NT, rows_smem(E, CB), s>>>(a);
+  k_fwd_rows<E, NT, CB, PF><<<g, NT, rows_smem(E, CB, PF), s>>>(a);
 }
 template <int CB>
 void rows_launch(const FwdArgs& a, int grid, cudaStream_t s) {
+  if constexpr (CB <= 12) {
+    if (a.rows_pf) {
+      rows_launch_e<CB, rows_pf_e<CB>(), true>(a, grid, s);
+      return;
+    }
+  }
   if constexpr (CB == 12) {
     if (a.rows14) {
       rows_launch_e<CB, 14>(a, grid, s);
@@ -580,11 +663,10 @@ cudaError_t cols_attr() {
   constexpr int NT = E < kPassElemsLog ? kPassThreads : kColsThreads;
   return cudaFuncSetAttribute(k_fwd_cols<NT, QB, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)cols_smem(E));
 }
-template <int CB, int E = rows_e<CB>()>
+template <int CB, int E = rows_e<CB>(), bool PF = false>
 cudaError_t rows_attr() {
-  constexpr int NT = E < kPassElemsLog ? kPassThreads : (E == kPassElemsLog ? kColsThreads : kPassThreadsWide);
-  return cudaFuncSetAttribute(k_fwd_rows<E, NT, CB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              (int)rows_smem(E, CB));
+  return cudaFuncSetAttribute(k_fwd_rows<E, rows_nt<E, PF>(), CB, PF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              (int)rows_smem(E, CB, PF));
 }
 
 // ================================================================ launchers
@@ -607,6 +689,10 @@ cudaError_t set_fwd_attributes() {
     if (e == cudaSuccess) e = rows_attr<decltype(C)::value>();
   });
   if (e == cudaSuccess) e = rows_attr<12, 14>();
+  static_for_host<9, 13>([&](auto C) {
+    constexpr int c = decltype(C)::value;
+    if (e == cudaSuccess) e = rows_attr<c, rows_pf_e<c>(), true>();
+  });
   static_for_host<9, 12>([&](auto C) {
     static_for_host<3, 10>([&](auto Q) {
       if (e == cudaSuccess)

@@ -67,6 +67,8 @@ struct FwdArgs {
   int in_real;
   float2* y;
   const SigDesc* sigs;
+  int nsigs;          // descriptors in sigs (work items are checked against it)
+  int nids;           // entries in sig_ids
   const int32_t* sig_ids;
   const void* items;  // TileItem* or LevelItem*
   int nitems;
@@ -75,6 +77,7 @@ struct FwdArgs {
   float2* scratch2;   // dual-level cols: the upper level's intermediate
   int cb_min;         // two-pass levels: C = 2^max(i - 12, cb_min), cb_min 9..11 (0 means 10)
   int rows14;         // C = 2^12 rows CTAs of 2^14 points (4 residues, 1 per SM) instead of 2^13
+  int rows_pf;        // rows CTAs that copy the children into shared memory when they start
   Twiddles tw;
   int* status;
 };
@@ -83,6 +86,8 @@ struct AdjArgs {
   const float2* gy;   // upstream gradient, same layout as y
   float2* gx;         // complex64 gradient of x
   const SigDesc* sigs;
+  int nsigs;          // descriptors in sigs (work items are checked against it)
+  int nids;           // entries in sig_ids
   const int32_t* sig_ids;
   const void* items;
   int nitems;
@@ -103,6 +108,38 @@ struct AdjArgs {
   const float2* t;
   double* loss;
 };
+
+// ---- work-item checks
+// Kernels check every work item against the signal descriptors before using
+// it; an item that does not describe a part of a planned signal (a work list
+// damaged in device memory) raises kStatusBadItem in the status word and the
+// block skips it, so that no access leaves the plan's buffers.
+__device__ __forceinline__ bool level_item_ok(const SigDesc* sigs, int nsigs, const LevelItem& it, int level,
+                                              int nblk, SigDesc& sd) {
+  if (it.sig < 0 || it.sig >= nsigs) return false;
+  sd = sigs[it.sig];
+  if (sd.m < level || sd.m > 26 || level < 1) return false;
+  if (it.window < 0 || (int64_t)it.window >= ((int64_t)1 << (sd.m - level))) return false;
+  return it.block >= 0 && it.block < nblk;
+}
+// the header of a tile item (before any signal of it is read)
+__device__ __forceinline__ bool tile_item_head_ok(const TileItem& it, int nids, int tile_log) {
+  const int n = it.nsig;
+  if (n < 1 || (n & (n - 1)) != 0 || it.tlog < 5 || it.tlog > tile_log) return false;
+  if (((int64_t)n << it.tlog) > ((int64_t)1 << tile_log)) return false;
+  if (it.tile < 0 || (n > 1 && it.tile != 0)) return false;
+  return it.sig_list >= 0 && (int64_t)it.sig_list + n <= nids;
+}
+// one signal of a tile item: a whole signal of 2^tlog when packed, else a
+// signal long enough to hold tile `tile`
+__device__ __forceinline__ bool tile_sig_ok(const SigDesc* sigs, int nsigs, int id, const TileItem& it,
+                                            SigDesc& sd) {
+  if (id < 0 || id >= nsigs) return false;
+  sd = sigs[id];
+  if (sd.m > 26) return false;
+  if (it.nsig > 1) return sd.m == it.tlog;
+  return sd.m >= it.tlog && ((int64_t)(it.tile + 1) << it.tlog) <= ((int64_t)1 << sd.m);
+}
 
 // launchers (defined in the .cu files)
 cudaError_t launch_fwd_tile(const FwdArgs& a, int grid, cudaStream_t s);

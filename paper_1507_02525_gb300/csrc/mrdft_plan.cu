@@ -26,6 +26,7 @@ namespace mrdft {
 cudaError_t set_fwd_attributes();
 cudaError_t set_adj_attributes();
 void set_global_error(const std::string& msg);
+mrdft_status noalloc_status_poll();
 }  // namespace mrdft
 
 using namespace mrdft;
@@ -61,6 +62,18 @@ struct Launch {
 // intermediate stay in L2 between the launches of the chain.
 struct Segment {
   std::vector<Launch> chain;  // tile launch first, then levels ascending
+  int parent = -1;            // forward tree: the top node over this segment, if any
+};
+
+// Forward tree of the levels above the segment size: one node per window of
+// such a level (its cols and rows launches over that window's items), run as
+// soon as its two children -- segments for the lowest top level, nodes above
+// -- have run, on the stream of the child enqueued last, so that it overlaps
+// the other chains and finds its children's spectra still in L2.
+struct TopNode {
+  Launch L;
+  int child[2];   // >= 0: segment index; < 0: node -(c + 1)
+  int parent = -1;
 };
 
 struct GraphKey {
@@ -69,13 +82,19 @@ struct GraphKey {
   cudaStream_t s;
   const void* t;  // fused loss gradient: targets and loss accumulator
   const void* l;
-  bool operator<(const GraphKey& o) const {
-    if (a != o.a) return a < o.a;
-    if (b != o.b) return b < o.b;
-    if (s != o.s) return s < o.s;
-    if (t != o.t) return t < o.t;
-    return l < o.l;
-  }
+  bool operator==(const GraphKey& o) const { return a == o.a && b == o.b && s == o.s && t == o.t && l == o.l; }
+};
+
+// Instantiated graphs of one direction, least recently used first out: at
+// most kGraphCacheMax per direction; a new (buffers, stream) key past that
+// limit re-targets the oldest executable graph with cudaGraphExecUpdate (the
+// launch sequence is the same, only the pointers differ) instead of
+// instantiating another one.
+constexpr size_t kGraphCacheMax = 4;
+struct GraphEntry {
+  GraphKey key;
+  cudaGraphExec_t exec;
+  uint64_t last_use;
 };
 
 std::mutex g_err_mu;
@@ -101,22 +120,29 @@ struct mrdft_plan_s {
   // device resources
   SigDesc* d_sigs = nullptr;
   int32_t* d_tile_ids = nullptr;
+  int n_tile_ids = 0;
   TileItem* d_tiles = nullptr;
   int n_tiles = 0;
   int32_t* d_tiny_ids = nullptr;
   int n_tiny = 0;
   LevelItem* d_levels = nullptr;
+  int64_t n_level_items = 0;
   std::vector<Segment> segments;
-  std::vector<Launch> top;  // levels above seg_log, ascending, whole plan
+  std::vector<Launch> top;  // levels above seg_log, ascending, whole plan (adjoint; forward without the tree)
+  std::vector<TopNode> top_nodes;   // forward tree (children before parents)
+  bool fwd_tree = true;             // off: the forward runs `top` after every segment instead
+  std::vector<cudaEvent_t> ev_seg, ev_node;
   int seg_log = 23;
   int nstreams = 4;
   bool seg_fixed = false;      // set by mrdft_plan_opts (else the environment may override)
   bool streams_fixed = false;
-  bool dual_cols = true;       // pair two-pass levels in one cols pass (MRDFT_DUAL_COLS=0: off)
-  int adj_rows13 = 1;          // adjoint C = 2^10 rows CTAs of 2^13 points (MRDFT_ADJ_ROWS13=0: 2^12)
-  int adj_cb_min = 10;         // adjoint two-pass levels: C = 2^max(i - 12, adj_cb_min) (MRDFT_ADJ_CB)
-  int fwd_rows14 = 1;          // forward C = 2^12 rows CTAs of 2^14 points (MRDFT_FWD_ROWS14=0: 2^13)
-  int fwd_cb_min = 9;          // forward two-pass levels: C = 2^max(i - 12, fwd_cb_min) (MRDFT_FWD_CB=10, 11)
+  // kernel variants (mrdft_exec_opts; none changes the result)
+  bool dual_cols = true;       // pair two-pass levels in one cols pass
+  int adj_rows13 = 1;          // adjoint C = 2^10 rows CTAs of 2^13 points (else 2^12)
+  int adj_cb_min = 10;         // adjoint two-pass levels: C = 2^max(i - 12, adj_cb_min)
+  int fwd_rows14 = 1;          // forward C = 2^12 rows CTAs of 2^14 points (else 2^13; last-pass children reads only)
+  int fwd_cb_min = 9;          // forward two-pass levels: C = 2^max(i - 12, fwd_cb_min)
+  int fwd_rows_pf = 1;         // forward rows CTAs prefetch the children into shared memory
   std::vector<cudaStream_t> workers;
   std::vector<cudaEvent_t> ev_join;
   cudaEvent_t ev_fork = nullptr;
@@ -137,7 +163,10 @@ struct mrdft_plan_s {
   void* d_stage_y = nullptr;
 
 
-  std::map<GraphKey, cudaGraphExec_t> fwd_graphs, adj_graphs;
+  std::vector<GraphEntry> fwd_graphs, adj_graphs;
+  uint64_t graph_clock = 0;
+  int64_t graph_captures = 0;   // stream captures made
+  int64_t graph_updates = 0;    // of which re-targeted an existing executable graph
   // adjoint launches of mrdft_loss_grad: targets and loss accumulator (else null)
   const float2* cur_t = nullptr;
   double* cur_loss = nullptr;
@@ -240,12 +269,18 @@ void release(mrdft_plan_s* p) {
   p->workers.clear();
   for (cudaEvent_t e : p->ev_join) cudaEventDestroy(e);
   p->ev_join.clear();
+  for (cudaEvent_t e : p->ev_seg)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_node)
+    if (e) cudaEventDestroy(e);
+  p->ev_seg.clear();
+  p->ev_node.clear();
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   p->ev_fork = nullptr;
   for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
   p->event_pool.clear();
-  for (auto& kv : p->fwd_graphs) cudaGraphExecDestroy(kv.second);
-  for (auto& kv : p->adj_graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& g : p->fwd_graphs) cudaGraphExecDestroy(g.exec);
+  for (auto& g : p->adj_graphs) cudaGraphExecDestroy(g.exec);
   p->fwd_graphs.clear();
   p->adj_graphs.clear();
   void* ptrs[] = {p->d_sigs, p->d_tile_ids, p->d_tiles, p->d_tiny_ids, p->d_levels,
@@ -303,18 +338,6 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
   if (!p->streams_fixed) {
     const char* env = getenv("MRDFT_STREAMS");
     if (env) p->nstreams = std::max(1, std::min(16, atoi(env)));
-  }
-  {
-    const char* env = getenv("MRDFT_DUAL_COLS");
-    if (env) p->dual_cols = atoi(env) != 0;
-    env = getenv("MRDFT_ADJ_ROWS13");
-    if (env) p->adj_rows13 = atoi(env) != 0;
-    env = getenv("MRDFT_ADJ_CB");
-    if (env) p->adj_cb_min = std::max(9, std::min(10, atoi(env)));
-    env = getenv("MRDFT_FWD_ROWS14");
-    if (env) p->fwd_rows14 = atoi(env) != 0;
-    env = getenv("MRDFT_FWD_CB");
-    if (env) p->fwd_cb_min = std::max(9, std::min(11, atoi(env)));
   }
   const int S = p->seg_log;
   const int64_t in_b = p->dtype == MRDFT_R32 ? 4 : 8;
@@ -454,7 +477,42 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     if (L.count) p->top.push_back(L);
   }
   pair_levels(p->top);
+  if (p->fwd_tree && !p->top.empty()) {
+    // segment of each (signal, level-S window) of the signals longer than a segment
+    std::map<std::pair<int32_t, int32_t>, int> seg_of;
+    for (size_t j = 0; j < seg_units.size(); ++j)
+      for (const Unit& u : seg_units[j])
+        if (p->sigs[u.sig].m > S) seg_of[{u.sig, u.w}] = (int)j;
+    for (int32_t sg : order) {
+      const int m = p->sigs[sg].m;
+      if (m <= S) continue;
+      std::vector<int> below;  // nodes (or segments) of the level just below, by window
+      for (int32_t w = 0; w < (int32_t)(int64_t(1) << (m - S)); ++w) below.push_back(seg_of.at({sg, w}));
+      for (int i = S + 1; i <= m; ++i) {
+        std::vector<int> here;
+        for (int64_t W = 0; W < (int64_t(1) << (m - i)); ++W) {
+          TopNode nd{};
+          nd.L.kind = i <= kWinMaxLog + 1 ? LK_WIN : LK_PASS;
+          nd.L.level = i;
+          nd.L.off = (int64_t)litems.size();
+          add_level_items(i, sg, W, 1, nd.L);
+          nd.L.count = (int)((int64_t)litems.size() - nd.L.off);
+          const int k = (int)p->top_nodes.size();
+          for (int c = 0; c < 2; ++c) {
+            nd.child[c] = i == S + 1 ? below[2 * W + c] : -(below[2 * W + c] + 1);
+            if (i == S + 1) p->segments[below[2 * W + c]].parent = k;
+            else p->top_nodes[below[2 * W + c]].parent = k;
+          }
+          p->top_nodes.push_back(nd);
+          here.push_back(k);
+        }
+        below.swap(here);
+      }
+    }
+  }
   p->n_tiles = (int)tiles.size();
+  p->n_tile_ids = (int)tile_ids.size();
+  p->n_level_items = (int64_t)litems.size();
   p->n_tiny = (int)tiny_ids.size();
 
   // streams and events for the concurrent segment chains
@@ -468,6 +526,14 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     p->ev_join.push_back(e);
   }
   MRDFT_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+  if (!p->top_nodes.empty()) {
+    p->ev_seg.assign(p->segments.size(), nullptr);
+    p->ev_node.assign(p->top_nodes.size(), nullptr);
+    for (size_t j = 0; j < p->segments.size(); ++j)
+      if (p->segments[j].parent >= 0) MRDFT_CUDA(p, cudaEventCreateWithFlags(&p->ev_seg[j], cudaEventDisableTiming));
+    for (size_t k = 0; k < p->top_nodes.size(); ++k)
+      MRDFT_CUDA(p, cudaEventCreateWithFlags(&p->ev_node[k], cudaEventDisableTiming));
+  }
 
   // ---- twiddles: FP64 on the host, rounded once
   std::vector<float2> tw13(1 << kTwLog), twlo(1 << kTwSplit), twhi(1 << (kTwBigLog - kTwSplit));
@@ -507,6 +573,7 @@ mrdft_status launch_fwd(mrdft_plan_s* p, FwdArgs a, const Launch& L, cudaStream_
   a.nitems = L.count;
   if (L.kind == LK_TILE) {
     a.sig_ids = p->d_tile_ids;
+    a.nids = p->n_tile_ids;
     a.items = p->d_tiles + L.off;
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_TILE, L.bytes, st, [&] { return launch_fwd_tile(a, L.count, st); }));
   } else if (L.kind == LK_WIN) {
@@ -540,27 +607,35 @@ mrdft_status launch_fwd(mrdft_plan_s* p, FwdArgs a, const Launch& L, cudaStream_
 
 // Fork the segment chains over the worker streams (event fork / join on the
 // caller's stream, which also works under stream capture).
-template <class F>
-mrdft_status run_segments(mrdft_plan_s* p, cudaStream_t st, F&& chain) {
+struct NoAfter {
+  mrdft_status operator()(size_t, cudaStream_t) const { return MRDFT_OK; }
+};
+template <class F, class A = NoAfter>
+mrdft_status run_segments(mrdft_plan_s* p, cudaStream_t st, F&& chain, A&& after = NoAfter{}) {
   const int nw = p->timing_serial ? 0 : (int)p->workers.size();
   if (nw <= 1) {
     for (size_t j = 0; j < p->segments.size(); ++j) {
       mrdft_status r = chain(p->segments[j], st);
+      if (r == MRDFT_OK) r = after(j, st);
       if (r != MRDFT_OK) return r;
     }
     return MRDFT_OK;
   }
   MRDFT_CUDA(p, cudaEventRecord(p->ev_fork, st));
   for (int k = 0; k < nw; ++k) MRDFT_CUDA(p, cudaStreamWaitEvent(p->workers[k], p->ev_fork, 0));
-  for (size_t j = 0; j < p->segments.size(); ++j) {
-    mrdft_status r = chain(p->segments[j], p->workers[j % nw]);
-    if (r != MRDFT_OK) return r;
+  mrdft_status r = MRDFT_OK;
+  for (size_t j = 0; j < p->segments.size() && r == MRDFT_OK; ++j) {
+    r = chain(p->segments[j], p->workers[j % nw]);
+    if (r == MRDFT_OK) r = after(j, p->workers[j % nw]);
   }
+  // join every worker back even after a failed launch, so that the caller's
+  // stream stays ordered after whatever was queued (and a capture can end)
   for (int k = 0; k < nw; ++k) {
-    MRDFT_CUDA(p, cudaEventRecord(p->ev_join[k], p->workers[k]));
-    MRDFT_CUDA(p, cudaStreamWaitEvent(st, p->ev_join[k], 0));
+    cudaError_t e = cudaEventRecord(p->ev_join[k], p->workers[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, p->ev_join[k], 0);
+    if (e != cudaSuccess && r == MRDFT_OK) r = cuda_fail(p, e, "joining the worker streams");
   }
-  return MRDFT_OK;
+  return r;
 }
 
 mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream_t st) {
@@ -569,25 +644,60 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
   a.in_real = p->dtype == MRDFT_R32;
   a.y = reinterpret_cast<float2*>(y);
   a.sigs = p->d_sigs;
+  a.nsigs = (int)p->nsig;
   a.scratch = p->d_scratch;
   a.cb_min = p->fwd_cb_min;
   a.rows14 = p->fwd_rows14;
+  a.rows_pf = p->fwd_rows_pf;
   a.tw = twiddles(p);
   a.status = p->d_status;
   if (p->n_tiny) {
     FwdArgs t = a;
     t.sig_ids = p->d_tiny_ids;
+    t.nids = p->n_tiny;
     t.nitems = p->n_tiny;
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_TINY, 0, st, [&] { return launch_fwd_tiny(t, p->n_tiny, st); }));
   }
-  mrdft_status r = run_segments(p, st, [&](const Segment& seg, cudaStream_t s) {
-    for (const Launch& L : seg.chain) {
-      mrdft_status q = launch_fwd(p, a, L, s);
+  const bool tree = !p->top_nodes.empty();
+  // forward tree: a node is enqueued right after the later of its two
+  // children, on that child's stream, after an event of the other child
+  std::vector<int> pending(p->top_nodes.size(), 2);
+  std::vector<cudaStream_t> done_on(p->top_nodes.size(), nullptr);
+  std::vector<cudaStream_t> seg_on(tree ? p->segments.size() : 0, nullptr);
+  auto child_done = [&](int parent, cudaStream_t s) -> mrdft_status {
+    while (parent >= 0 && --pending[parent] == 0) {
+      const TopNode& nd = p->top_nodes[parent];
+      for (int c = 0; c < 2; ++c) {  // the child on another stream: wait for its event
+        const int ch = nd.child[c];
+        const cudaStream_t cs = ch >= 0 ? seg_on[ch] : done_on[-ch - 1];
+        const cudaEvent_t ev = ch >= 0 ? p->ev_seg[ch] : p->ev_node[-ch - 1];
+        if (cs != s) MRDFT_CUDA(p, cudaStreamWaitEvent(s, ev, 0));
+      }
+      mrdft_status q = launch_fwd(p, a, nd.L, s);
       if (q != MRDFT_OK) return q;
+      done_on[parent] = s;
+      if (nd.parent >= 0) MRDFT_CUDA(p, cudaEventRecord(p->ev_node[parent], s));
+      parent = nd.parent;
     }
     return MRDFT_OK;
-  });
+  };
+  mrdft_status r = run_segments(
+      p, st,
+      [&](const Segment& seg, cudaStream_t s) {
+        for (const Launch& L : seg.chain) {
+          mrdft_status q = launch_fwd(p, a, L, s);
+          if (q != MRDFT_OK) return q;
+        }
+        return MRDFT_OK;
+      },
+      [&](size_t j, cudaStream_t s) -> mrdft_status {
+        if (!tree || p->segments[j].parent < 0) return MRDFT_OK;
+        seg_on[j] = s;
+        MRDFT_CUDA(p, cudaEventRecord(p->ev_seg[j], s));
+        return child_done(p->segments[j].parent, s);
+      });
   if (r != MRDFT_OK) return r;
+  if (tree) return MRDFT_OK;
   for (const Launch& L : p->top) {
     r = launch_fwd(p, a, L, st);
     if (r != MRDFT_OK) return r;
@@ -605,6 +715,7 @@ mrdft_status launch_adj(mrdft_plan_s* p, AdjArgs a, const Launch& L, cudaStream_
   a.nitems = L.count;
   if (L.kind == LK_TILE) {
     a.sig_ids = p->d_tile_ids;
+    a.nids = p->n_tile_ids;
     a.items = p->d_tiles + L.off;
     a.e_in = (!in_top && S == kTileLog && p->d_etop) ? p->d_etop : ebuf(kTileLog + 1);
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_TILE, L.bytes, st, [&] { return launch_adj_tile(a, L.count, st); }));
@@ -648,6 +759,7 @@ mrdft_status enqueue_adjoint(mrdft_plan_s* p, const void* gy, void* gx, cudaStre
   a.gy = reinterpret_cast<const float2*>(gy);
   a.gx = reinterpret_cast<float2*>(gx);
   a.sigs = p->d_sigs;
+  a.nsigs = (int)p->nsig;
   a.acc = p->d_acc;
   a.scratch = p->d_scratch;
   a.tw = twiddles(p);
@@ -669,6 +781,7 @@ mrdft_status enqueue_adjoint(mrdft_plan_s* p, const void* gy, void* gx, cudaStre
   if (p->n_tiny) {
     AdjArgs t = a;
     t.sig_ids = p->d_tiny_ids;
+    t.nids = p->n_tiny;
     t.nitems = p->n_tiny;
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_TINY, 0, st, [&] { return launch_adj_tiny(t, p->n_tiny, st); }));
   }
@@ -677,38 +790,65 @@ mrdft_status enqueue_adjoint(mrdft_plan_s* p, const void* gy, void* gx, cudaStre
 
 using Enqueue = mrdft_status (*)(mrdft_plan_s*, const void*, void*, cudaStream_t);
 
-mrdft_status run(mrdft_plan_s* p, std::map<GraphKey, cudaGraphExec_t>& cache, Enqueue fn,
-                 const void* in, void* out, cudaStream_t st) {
+
+mrdft_status run(mrdft_plan_s* p, std::vector<GraphEntry>& cache, Enqueue fn, const void* in, void* out,
+                 cudaStream_t st) {
   int dev = -1;
   MRDFT_CUDA(p, cudaGetDevice(&dev));
   if (dev != p->device) return fail(p, MRDFT_EINVAL, "plan used on a different device than it was created on");
   if (!(p->flags & MRDFT_FLAG_GRAPH) || p->timing) return fn(p, in, out, st);
   const GraphKey key{in, out, st, p->cur_t, p->cur_loss};
-  auto found = cache.find(key);
-  if (found == cache.end()) {
-    cudaStream_t cap = st;
-    bool own = false;
-    if (cap == nullptr) {  // the legacy stream cannot be captured
-      MRDFT_CUDA(p, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-      own = true;
+  for (GraphEntry& g : cache) {
+    if (g.key == key) {
+      g.last_use = ++p->graph_clock;
+      MRDFT_CUDA(p, cudaGraphLaunch(g.exec, st));
+      return MRDFT_OK;
     }
-    MRDFT_CUDA(p, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
-    mrdft_status s = fn(p, in, out, cap);
-    cudaGraph_t g = nullptr;
-    cudaError_t e = cudaStreamEndCapture(cap, &g);
-    if (own) cudaStreamDestroy(cap);
-    if (s != MRDFT_OK) {
-      if (g) cudaGraphDestroy(g);
-      return s;
-    }
-    if (e != cudaSuccess) return cuda_fail(p, e, "cudaStreamEndCapture");
-    cudaGraphExec_t ex = nullptr;
-    e = cudaGraphInstantiate(&ex, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(p, e, "cudaGraphInstantiate");
-    found = cache.emplace(key, ex).first;
   }
-  MRDFT_CUDA(p, cudaGraphLaunch(found->second, st));
+  cudaStream_t cap = st;
+  bool own = false;
+  if (cap == nullptr) {  // the legacy stream cannot be captured
+    MRDFT_CUDA(p, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    own = true;
+  }
+  MRDFT_CUDA(p, cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+  mrdft_status s = fn(p, in, out, cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(cap, &graph);
+  if (own) cudaStreamDestroy(cap);
+  if (s != MRDFT_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(p, e, "cudaStreamEndCapture");
+  ++p->graph_captures;
+  cudaGraphExec_t ex = nullptr;
+  if (cache.size() >= kGraphCacheMax) {
+    size_t old = 0;
+    for (size_t j = 1; j < cache.size(); ++j)
+      if (cache[j].last_use < cache[old].last_use) old = j;
+    cudaGraphExecUpdateResultInfo info{};
+    if (cudaGraphExecUpdate(cache[old].exec, graph, &info) == cudaSuccess) {
+      ex = cache[old].exec;
+      cache[old].key = key;
+      cache[old].last_use = ++p->graph_clock;
+      ++p->graph_updates;
+    } else {
+      (void)cudaGetLastError();
+      cudaGraphExecDestroy(cache[old].exec);
+      cache.erase(cache.begin() + (std::ptrdiff_t)old);
+    }
+  }
+  if (!ex) {
+    e = cudaGraphInstantiate(&ex, graph, 0);
+    if (e != cudaSuccess) {
+      cudaGraphDestroy(graph);
+      return cuda_fail(p, e, "cudaGraphInstantiate");
+    }
+    cache.push_back(GraphEntry{key, ex, ++p->graph_clock});
+  }
+  cudaGraphDestroy(graph);
+  MRDFT_CUDA(p, cudaGraphLaunch(ex, st));
   return MRDFT_OK;
 }
 
@@ -725,11 +865,28 @@ mrdft_status mrdft_plan(mrdft_plan_t* out, const int64_t* lengths, int64_t n_len
 
 mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t n_lengths, int64_t batch,
                              int dtype, uint32_t flags, int32_t seg_log, int32_t streams) {
+  mrdft_exec_opts o{};
+  o.seg_log = seg_log;
+  o.streams = streams;
+  return mrdft_plan_ex(out, lengths, n_lengths, batch, dtype, flags, &o);
+}
+
+mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_lengths, int64_t batch, int dtype,
+                           uint32_t flags, const mrdft_exec_opts* opts) {
   if (!out) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: out is NULL");
-  if (seg_log != 0 && (seg_log < kTileLog || seg_log > kMaxLog))
-    return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_opts: seg_log must be 0 or in [12, 26]");
-  if (streams < 0 || streams > 16) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_opts: streams must be in [0, 16]");
   *out = nullptr;
+  mrdft_exec_opts o{};
+  if (opts) o = *opts;
+  auto sw = [](int32_t v) { return v == MRDFT_OPT_DEFAULT || v == MRDFT_OPT_OFF || v == MRDFT_OPT_ON; };
+  if (o.seg_log != 0 && (o.seg_log < kTileLog || o.seg_log > kMaxLog))
+    return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: seg_log must be 0 or in [12, 26]");
+  if (o.streams < 0 || o.streams > 16) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: streams must be in [0, 16]");
+  if (o.fwd_cb != 0 && (o.fwd_cb < 9 || o.fwd_cb > 11))
+    return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: fwd_cb must be 0 or in [9, 11]");
+  if (o.adj_cb != 0 && (o.adj_cb < 9 || o.adj_cb > 10))
+    return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: adj_cb must be 0 or in [9, 10]");
+  if (!sw(o.fwd_rows_prefetch) || !sw(o.fwd_rows14) || !sw(o.adj_rows13) || !sw(o.dual_cols) || !sw(o.fwd_tree))
+    return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: switches must be MRDFT_OPT_DEFAULT, _OFF or _ON");
   if (!lengths) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: lengths is NULL");
   if (batch < 1 || batch > (int64_t(1) << 30))
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: batch must be in [1, 2^30]");
@@ -750,14 +907,22 @@ mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t 
   if (!p) return fail(nullptr, MRDFT_ENOMEM, "mrdft_plan: host allocation failed");
   p->dtype = dtype;
   p->flags = flags;
-  if (seg_log) {
-    p->seg_log = seg_log;
+  if (o.seg_log) {
+    p->seg_log = o.seg_log;
     p->seg_fixed = true;
   }
-  if (streams) {
-    p->nstreams = streams;
+  if (o.streams) {
+    p->nstreams = o.streams;
     p->streams_fixed = true;
   }
+  auto on = [](int32_t v, bool dflt) { return v == MRDFT_OPT_DEFAULT ? dflt : v == MRDFT_OPT_ON; };
+  if (o.fwd_cb) p->fwd_cb_min = o.fwd_cb;
+  if (o.adj_cb) p->adj_cb_min = o.adj_cb;
+  p->fwd_rows_pf = on(o.fwd_rows_prefetch, p->fwd_rows_pf != 0);
+  p->fwd_rows14 = on(o.fwd_rows14, p->fwd_rows14 != 0);
+  p->adj_rows13 = on(o.adj_rows13, p->adj_rows13 != 0);
+  p->dual_cols = on(o.dual_cols, p->dual_cols);
+  p->fwd_tree = on(o.fwd_tree, p->fwd_tree);
   mrdft_status st = build_plan(p, lengths, n_lengths, batch);
   if (st != MRDFT_OK) {
     fail(nullptr, st, p->err);
@@ -766,6 +931,21 @@ mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t 
     return st;
   }
   *out = p;
+  return MRDFT_OK;
+}
+
+mrdft_status mrdft_plan_get_opts(mrdft_plan_t p, mrdft_exec_opts* opts) {
+  if (!p || !opts) return fail(p, MRDFT_EINVAL, "mrdft_plan_get_opts: NULL argument");
+  auto sw = [](bool v) { return v ? MRDFT_OPT_ON : MRDFT_OPT_OFF; };
+  opts->seg_log = p->seg_log;
+  opts->streams = p->nstreams;
+  opts->fwd_cb = p->fwd_cb_min;
+  opts->adj_cb = p->adj_cb_min;
+  opts->fwd_rows_prefetch = sw(p->fwd_rows_pf != 0);
+  opts->fwd_rows14 = sw(p->fwd_rows14 != 0);
+  opts->adj_rows13 = sw(p->adj_rows13 != 0);
+  opts->dual_cols = sw(p->dual_cols);
+  opts->fwd_tree = sw(p->fwd_tree);
   return MRDFT_OK;
 }
 
@@ -835,7 +1015,7 @@ mrdft_status mrdft_forward_host(mrdft_plan_t p, const void* x_host, void* y_host
 }
 
 mrdft_status mrdft_status_poll(mrdft_plan_t p) {
-  if (!p) return fail(nullptr, MRDFT_EINVAL, "mrdft_status_poll: plan is NULL");
+  if (!p) return noalloc_status_poll();
   int v = 0;
   MRDFT_CUDA(p, cudaDeviceSynchronize());
   MRDFT_CUDA(p, cudaMemcpy(&v, p->d_status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -867,7 +1047,14 @@ mrdft_status mrdft_plan_info(mrdft_plan_t p, int32_t* tile_log, int32_t* fwd_lau
   };
   for (const Segment& g : p->segments)
     for (const Launch& L : g.chain) count(L);
-  for (const Launch& L : p->top) count(L);
+  if (p->top_nodes.empty()) {
+    for (const Launch& L : p->top) count(L);
+  } else {
+    const int n_keep = n;
+    for (const Launch& L : p->top) count(L);
+    n = n_keep;
+    for (const TopNode& nd : p->top_nodes) n += nd.L.kind == LK_PASS ? 2 : 1;
+  }
   if (tile_log) *tile_log = kTileLog;
   if (fwd_launches) *fwd_launches = n;
   if (adj_launches) *adj_launches = na;
@@ -894,6 +1081,30 @@ mrdft_status mrdft_timing_read(mrdft_plan_t p, int kind, double* ms, int64_t* la
   if (ms) *ms = p->t_ms[kind];
   if (launches) *launches = p->t_launches[kind];
   if (bytes) *bytes = p->t_bytes[kind];
+  return MRDFT_OK;
+}
+
+mrdft_status mrdft_plan_graph_stats(mrdft_plan_t p, int32_t* cached, int64_t* captures, int64_t* updates) {
+  if (!p) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_graph_stats: plan is NULL");
+  if (cached) *cached = (int32_t)(p->fwd_graphs.size() + p->adj_graphs.size());
+  if (captures) *captures = p->graph_captures;
+  if (updates) *updates = p->graph_updates;
+  return MRDFT_OK;
+}
+
+mrdft_status mrdft_debug_item(mrdft_plan_t p, int list, int64_t index, const int32_t* new_fields,
+                              int32_t* old_fields) {
+  if (!p) return fail(nullptr, MRDFT_EINVAL, "mrdft_debug_item: plan is NULL");
+  if (list != 0 && list != 1) return fail(p, MRDFT_EINVAL, "mrdft_debug_item: list must be 0 (tiles) or 1 (levels)");
+  const int64_t n = list == 0 ? p->n_tiles : p->n_level_items;
+  if (index < 0 || index >= n) return fail(p, MRDFT_EINVAL, "mrdft_debug_item: index out of range");
+  static_assert(sizeof(TileItem) == 16 && sizeof(LevelItem) == 16, "work items are four 32-bit words");
+  void* dev = list == 0 ? static_cast<void*>(p->d_tiles + index) : static_cast<void*>(p->d_levels + index);
+  int32_t cur[4];
+  MRDFT_CUDA(p, cudaDeviceSynchronize());
+  MRDFT_CUDA(p, cudaMemcpy(cur, dev, sizeof(cur), cudaMemcpyDeviceToHost));
+  if (old_fields) std::memcpy(old_fields, cur, sizeof(cur));
+  if (new_fields) MRDFT_CUDA(p, cudaMemcpy(dev, new_fields, sizeof(cur), cudaMemcpyHostToDevice));
   return MRDFT_OK;
 }
 

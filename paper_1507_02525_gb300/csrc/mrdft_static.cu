@@ -18,6 +18,7 @@
 namespace mrdft {
 cudaError_t set_fwd_attributes();
 void set_global_error(const std::string& msg);
+mrdft_status noalloc_status_poll();
 }  // namespace mrdft
 
 using namespace mrdft;
@@ -143,6 +144,29 @@ mrdft_status fail_na(mrdft_status s, const std::string& msg) {
 
 }  // namespace
 
+// mrdft_status_poll(NULL): read and clear the device status word of the
+// allocation-free entry point on the current device (MRDFT_OK when that entry
+// point has not run there).  Waits for the device.
+mrdft_status mrdft::noalloc_status_poll() {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail_na(MRDFT_ECUDA, std::string("status poll: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail_na(MRDFT_EUNSUPPORTED, "status poll: device index out of range");
+  int* status = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (!g_dev[dev].ready) return MRDFT_OK;
+    status = g_dev[dev].status;
+  }
+  int v = 0;
+  if ((e = cudaDeviceSynchronize()) == cudaSuccess && (e = cudaMemcpy(&v, status, sizeof(int), cudaMemcpyDeviceToHost)) == cudaSuccess)
+    e = cudaMemset(status, 0, sizeof(int));
+  if (e != cudaSuccess) return fail_na(MRDFT_ECUDA, std::string("status poll: ") + cudaGetErrorString(e));
+  if (v == kStatusTimeout) return fail_na(MRDFT_ETIMEOUT, "a device-side wait gave up");
+  if (v != 0) return fail_na(MRDFT_EDEVICE, "a kernel flagged an invalid work item (code " + std::to_string(v) + ")");
+  return MRDFT_OK;
+}
+
 extern "C" mrdft_status mrdft_forward_noalloc(const void* x, void* y, int64_t n, mrdft_stream_t stream) {
   if (!x || !y) return fail_na(MRDFT_EINVAL, "x or y is NULL");
   if (((reinterpret_cast<uintptr_t>(x) | reinterpret_cast<uintptr_t>(y)) & 15) != 0)
@@ -171,6 +195,8 @@ extern "C" mrdft_status mrdft_forward_noalloc(const void* x, void* y, int64_t n,
   a.in_real = 0;
   a.y = reinterpret_cast<float2*>(y);
   a.sigs = st->sigs;
+  a.nsigs = kMaxLogNA + 1;
+  a.nids = kMaxLogNA + 1;
   a.scratch = st->scratch;
   a.tw = Twiddles{st->tw13, st->twlo, st->twhi};
   a.status = st->status;

@@ -77,7 +77,11 @@ def test_null_arguments(lib):
     assert lib.mrdft_adjoint(None, None, None, None) == 1
     assert lib.mrdft_forward_host(None, None, None, None) == 1
     assert lib.mrdft_loss_grad(None, None, None, None, None, None, None) == 1
-    assert lib.mrdft_status_poll(None) == 1
+    # NULL polls the allocation-free entry point's status word: OK where it
+    # never ran, ECUDA where there is no device to ask
+    assert lib.mrdft_status_poll(None) in (0, 3)
+    assert lib.mrdft_plan_graph_stats(None, None, None, None) == 1
+    assert lib.mrdft_debug_item(None, 1, 0, None, None) == 1
     n = ctypes.c_int64()
     assert lib.mrdft_output_elems(None, ctypes.byref(n)) == 1
     assert lib.mrdft_plan_info(None, None, None, None) == 1
@@ -97,3 +101,27 @@ def test_api_refuses_cpu_tensors():
     from paper_1507_02525_gb300 import api
     with pytest.raises(ValueError):
         api.mrdft(torch.zeros(16, dtype=torch.complex64))
+
+
+@pytest.mark.parametrize("field,value", [("seg_log", 11), ("seg_log", 27), ("streams", 17), ("fwd_cb", 8),
+                                         ("fwd_cb", 12), ("adj_cb", 11), ("fwd_rows_prefetch", 3),
+                                         ("dual_cols", -1), ("fwd_tree", 7), ("adj_rows13", 5)])
+def test_plan_ex_rejects_bad_options(lib, field, value):
+    """Every execution option is range-checked before any device work."""
+    from paper_1507_02525_gb300 import _lib
+    h = ctypes.c_void_p()
+    arr = (ctypes.c_int64 * 1)(1 << 16)
+    o = _lib.ExecOpts()
+    setattr(o, field, value)
+    assert lib.mrdft_plan_ex(ctypes.byref(h), arr, 1, 1, 0, 0, ctypes.byref(o)) == 1
+    assert h.value is None
+    assert "mrdft_plan_ex" in lib.mrdft_last_error(None).decode()
+
+
+def test_exec_opts_from_dict():
+    from paper_1507_02525_gb300 import _lib
+    o = _lib.ExecOpts.from_dict({"seg_log": 21, "dual_cols": False, "fwd_tree": True, "fwd_cb": 10})
+    assert (o.seg_log, o.dual_cols, o.fwd_tree, o.fwd_cb, o.streams) == (21, _lib.OPT_OFF, _lib.OPT_ON, 10, 0)
+    assert o.to_dict()["fwd_rows_prefetch"] is None
+    with pytest.raises(ValueError):
+        _lib.ExecOpts.from_dict({"tile_log": 13})

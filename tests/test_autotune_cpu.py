@@ -82,3 +82,46 @@ def test_objective_is_part_of_the_key(tmp_path, monkeypatch):
     assert autotune.tune([1 << 24], 1, timer=lambda s, k: 1 / 0, adjoint=False) == (22, 2)
     with pytest.raises(ValueError):
         autotune.tune([1 << 24], 1, timer=lambda s, k: 1.0, objective="sideways")
+
+
+def test_tune_plan_searches_kernel_variants(tmp_path, monkeypatch):
+    """Shape first, then each kernel variant in turn on the best shape; a
+    variant is kept only when clearly faster; the choice is cached per
+    objective under its own key."""
+    monkeypatch.setenv("MRDFT_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    seen = []
+
+    def timer(o):
+        seen.append(dict(o))
+        ms = abs(o["seg_log"] - 21) + 0.1 * o["streams"] + 5.0
+        ms -= 0.5 if o.get("fwd_cb") == 10 else 0.0       # clearly faster: kept
+        ms -= 0.001 if o.get("dual_cols") is False else 0.0  # within the margin: not kept
+        ms -= 0.3 if o.get("fwd_tree") is False else 0.0
+        return ms
+
+    best = autotune.tune_plan([1 << 24], 1, objective="forward", timer=timer,
+                              candidates=[(20, 4), (21, 2), (22, 4)])
+    assert best == {"seg_log": 21, "streams": 2, "fwd_cb": 10, "fwd_tree": False}
+    names = {k for o in seen for k in o}
+    assert {"fwd_cb", "fwd_rows_prefetch", "dual_cols", "fwd_tree"} <= names
+    assert not any("adj_cb" in o for o in seen)
+    n = len(seen)
+    assert autotune.tune_plan([1 << 24], 1, objective="forward", timer=lambda o: 1 / 0) == best
+    assert len(seen) == n  # cached
+    adj = autotune.tune_plan([1 << 24], 1, objective="adjoint", timer=lambda o: float(o.get("adj_cb", 10)),
+                             candidates=[(21, 2)])
+    assert adj == {"seg_log": 21, "streams": 2, "adj_cb": 9}
+    data = json.loads((tmp_path / "tune.json").read_text())
+    assert sum(1 for k in data if k.endswith("|forward|opts")) == 1
+    assert sum(1 for k in data if k.endswith("|adjoint|opts")) == 1
+
+
+def test_knobs_only_where_they_change_the_plan():
+    # no two-pass levels: nothing to tune beyond the shape
+    assert autotune.knobs_for("forward", [1 << 14] * 8, 23) == ()
+    # two-pass levels, but every signal fits in a segment: no tree switch
+    names = [k for k, _ in autotune.knobs_for("forward", [1 << 18] * 64, 23)]
+    assert "fwd_tree" not in names and "fwd_cb" in names
+    assert "fwd_tree" in [k for k, _ in autotune.knobs_for("forward", [1 << 24], 21)]
+    both = [k for k, _ in autotune.knobs_for("both", [1 << 24], 21)]
+    assert both.count("dual_cols") == 1 and "adj_cb" in both and "fwd_cb" in both

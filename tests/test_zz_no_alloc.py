@@ -1,12 +1,15 @@
-"""The allocation-free entry point, mrdft_forward_noalloc, against mrdft_forward.
+"""The allocation-free entry point, mrdft_forward_noalloc, against the FP64
+oracle and against mrdft_forward.
 
 mrdft_forward_noalloc serves callers that must not call cudaMalloc (an
 external memory manager owns all device memory, or a hot loop cannot afford
 an allocation's implicit synchronisation): it keeps the two-pass levels'
-intermediate in a fixed device array instead of plan-owned scratch.  Its
-output must match the planned forward to the same tolerance the parity tests
-use, and two calls in a row must both be right (the shared scratch keeps the
-previous call's contents).  This file is collected last on purpose.
+intermediate in a fixed device array instead of plan-owned scratch.  Every
+level of its output must match the oracle within the parity tolerance, and
+the planned forward too; two calls in a row must both be right (the shared
+array keeps the previous call's contents); and its device status word, read
+with mrdft_status_poll(NULL), must report no skipped work item.  This file is
+collected last on purpose.
 """
 import ctypes
 
@@ -51,6 +54,12 @@ def _noalloc(x):
     return y.cpu().numpy()
 
 
+def _poll_noalloc():
+    lib = _lib.load()
+    st = lib.mrdft_status_poll(None)
+    assert st == _lib.MRDFT_OK, lib.mrdft_last_error(None).decode()
+
+
 def _close(y_new, y_ref, x):
     m = x.size.bit_length() - 1
     xn = float(np.linalg.norm(x.astype(np.complex128)))
@@ -62,16 +71,18 @@ def _close(y_new, y_ref, x):
         assert np.abs(d).max() <= ABS_FRAC * xn, f"level {i + 1}"
 
 
-@pytest.mark.parametrize("m", [16, 15, 14, 13, 10, 5, 3, 1])
-def test_noalloc_matches_forward_twice(m):
+@pytest.mark.parametrize("m", [16, 15, 14, 13, 12, 10, 5, 4, 3, 1])
+def test_noalloc_matches_oracle_and_forward_twice(oracle, m):
     n = 1 << m
     xa = inputs.complex_signals(1, n, seed=900 + m)[0]
     xb = inputs.complex_signals(1, n, seed=950 + m)[0]
     ya1 = _noalloc(xa)
     yb = _noalloc(xb)  # second call in a row, other data, same shared scratch
     ya2 = _noalloc(xa)
-    _close(ya1, _planned(xa), xa)
-    _close(yb, _planned(xb), xb)
+    _poll_noalloc()
+    for y, x in ((ya1, xa), (yb, xb)):
+        _close(y, oracle.forward(x.astype(np.complex128)).reshape(-1), x)
+        _close(y, _planned(x), x)
     np.testing.assert_array_equal(ya1, ya2)
 
 
