@@ -63,6 +63,14 @@ typedef enum {
 /* Plan flags. */
 #define MRDFT_FLAG_GRAPH 1u /* replay a CUDA graph of the launch sequence (captured
                                on the first call for each (input, output) pair) */
+/* MRDFT_FLAG_BITREV: mrdft_forward stores every window in the order of the
+ * paper's Sec. 3 before the permutation Gamma: position p of a window of
+ * level i holds bin bitrev_i(p) (y_window = T_{2^i} Y_window, T the bit
+ * reversal over i bits).  The bins are computed in natural order and each
+ * window is then permuted in place (a read and a write of y), so this layout
+ * costs more than the natural one.  Forward only: mrdft_adjoint and
+ * mrdft_loss_grad return MRDFT_EUNSUPPORTED on such plans. */
+#define MRDFT_FLAG_BITREV 2u
 
 /*
  * mrdft_plan -- validate the signal lengths and allocate everything a
@@ -110,14 +118,20 @@ mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t 
  *   fwd_cb   : forward two-pass split h = Q C, C = 2^max(i - 12, fwd_cb), 9..11 (default 9)
  *   adj_cb   : adjoint two-pass split, 9..10 (default 10)
  *   fwd_rows_prefetch : forward rows CTAs copy the children spectra into
- *              shared memory when they start (default on)
+ *              shared memory when they start (default off)
  *   fwd_rows14 : with prefetch off, C = 2^12 forward rows CTAs of 2^14
  *              points instead of 2^13 (default on)
  *   adj_rows13 : adjoint C = 2^10 rows CTAs of 2^13 points instead of 2^12 (default on)
  *   dual_cols : consecutive two-pass levels of a chain share one cols pass (default on)
  *   fwd_tree : the forward runs each window of a level above the segment
- *              size as soon as its two children are done (default on);
- *              off: those levels run level by level after every segment
+ *              size as soon as its two children are done; off (default):
+ *              those levels run level by level after every segment
+ *   tile_first : the in-tile levels of every segment run as one launch,
+ *              before the segments (forward) or after them (adjoint),
+ *              instead of one launch per segment (default off)
+ *   tile_lean : forward tile CTAs that fit three to an SM (the FFT work
+ *              area shares the level buffer, twiddles read through L1)
+ *              instead of two (default off)
  */
 #define MRDFT_OPT_DEFAULT 0
 #define MRDFT_OPT_OFF 1
@@ -132,6 +146,8 @@ typedef struct {
   int32_t adj_rows13;
   int32_t dual_cols;
   int32_t fwd_tree;
+  int32_t tile_first;
+  int32_t tile_lean;
 } mrdft_exec_opts;
 
 /*

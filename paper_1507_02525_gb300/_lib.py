@@ -23,6 +23,7 @@ MRDFT_EDEVICE = 6
 MRDFT_C64 = 0
 MRDFT_R32 = 1
 MRDFT_FLAG_GRAPH = 1
+MRDFT_FLAG_BITREV = 2
 
 STATUS_NAMES = {0: "MRDFT_OK", 1: "MRDFT_EINVAL", 2: "MRDFT_ENOMEM", 3: "MRDFT_ECUDA",
                 4: "MRDFT_EUNSUPPORTED", 5: "MRDFT_ETIMEOUT", 6: "MRDFT_EDEVICE"}
@@ -44,8 +45,9 @@ OPT_DEFAULT, OPT_OFF, OPT_ON = 0, 1, 2
 class ExecOpts(ctypes.Structure):
     """mrdft_exec_opts (include/mrdft.h): 0 = library default; switches 1 = off, 2 = on."""
     _fields_ = [(n, ctypes.c_int32) for n in ("seg_log", "streams", "fwd_cb", "adj_cb", "fwd_rows_prefetch",
-                                               "fwd_rows14", "adj_rows13", "dual_cols", "fwd_tree")]
-    SWITCHES = ("fwd_rows_prefetch", "fwd_rows14", "adj_rows13", "dual_cols", "fwd_tree")
+                                               "fwd_rows14", "adj_rows13", "dual_cols", "fwd_tree", "tile_first",
+                                               "tile_lean")]
+    SWITCHES = ("fwd_rows_prefetch", "fwd_rows14", "adj_rows13", "dual_cols", "fwd_tree", "tile_first", "tile_lean")
 
     @classmethod
     def from_dict(cls, d):
@@ -145,7 +147,7 @@ class Plan:
 
     def __init__(self, lengths, batch: int | None = None, real_input: bool = False,
                  graph: bool = False, seg_log: int | None = None, streams: int | None = None,
-                 opts: dict | None = None):
+                 opts: dict | None = None, bitrev: bool = False):
         """``opts``: execution options by name (mrdft_exec_opts); ``seg_log`` and
         ``streams`` are shorthands for two of them."""
         lib = load()
@@ -162,7 +164,8 @@ class Plan:
         eo = ExecOpts.from_dict(o)
         st = lib.mrdft_plan_ex(ctypes.byref(h), arr, len(lengths), int(batch),
                                MRDFT_R32 if real_input else MRDFT_C64,
-                               MRDFT_FLAG_GRAPH if graph else 0, ctypes.byref(eo))
+                               (MRDFT_FLAG_GRAPH if graph else 0) | (MRDFT_FLAG_BITREV if bitrev else 0),
+                               ctypes.byref(eo))
         check(st, None)
         self._h = h
         self._lib = lib

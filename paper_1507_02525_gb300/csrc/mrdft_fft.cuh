@@ -70,13 +70,24 @@ __device__ __forceinline__ float2 twq(const TwQ& t, int e) {
 // w_{2^l}^e for l <= TB
 __device__ __forceinline__ float2 twq_l(const TwQ& t, int l, int e) { return twq(t, e << (t.TB - l)); }
 
+// The same twiddles read straight from the global table w_{2^14}^e (through
+// L1), for kernels that keep no per-CTA copy in shared memory.
+struct TwG {
+  const float2* t14;
+  int TB;
+};
+__device__ __forceinline__ float2 twq(const TwG& t, int e) {
+  return __ldg(&t.t14[(e << (kTwLog - t.TB)) & ((1 << kTwLog) - 1)]);
+}
+__device__ __forceinline__ float2 twq_l(const TwG& t, int l, int e) { return twq(t, e << (t.TB - l)); }
+
 // w^(k * step), k = 0 .. R-1, from one table entry (w^step) and products of
 // it (at most four extra roundings, far inside the FP32 error budget): one
 // lookup instead of log2(R) keeps the table-index and quadrant arithmetic off
 // the critical path of every butterfly group.
 __device__ __forceinline__ float2 csq(float2 a) { return make_float2(fmaf(a.x, a.x, -a.y * a.y), 2.f * a.x * a.y); }
-template <int R>
-__device__ __forceinline__ void twiddle_set(const TwQ& tw, int step, float2 (&w)[R]) {
+template <int R, class TW>
+__device__ __forceinline__ void twiddle_set(const TW& tw, int step, float2 (&w)[R]) {
   w[0] = make_float2(1.f, 0.f);
   if constexpr (R >= 2) w[1] = twq(tw, step);
   if constexpr (R >= 4) {
@@ -116,9 +127,9 @@ __device__ __forceinline__ int drev8(int v, int d) {
 // in place; PTS bounds the points per thread (NT * PTS >= points per pass).
 constexpr int kPreNone = 0, kPreBarrier = 1, kPreGroup = 2, kPreHalf = 3;
 
-template <int RB, int NT, int PTS, bool SEQ_MINOR, bool FIRST, bool LAST, int PRE, int ZS, bool GSRC, class Src,
-          class Pre, class Sink>
-__device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq_log, int SH, int P, const TwQ& tw,
+template <int RB, int NT, int PTS, bool SEQ_MINOR, bool FIRST, bool LAST, int PRE, int ZS, bool GSRC, class TW,
+          class Src, class Pre, class Sink>
+__device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq_log, int SH, int P, const TW& tw,
                                         Src&& src, Pre&& pre, Sink&& sink) {
   constexpr int R = 1 << RB;
   constexpr int GMAX = (PTS >> RB) > 0 ? (PTS >> RB) : 1;  // groups per thread
@@ -211,9 +222,9 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
 //   src(b, n) -> float2, or with GSRC src(b, n0, LRB, float2 (&v)[R], IC<RB>)
 //   filling the R first-pass inputs n0 + (r << LRB) of a group at once;
 //   pre(slot, b, k) (PRE != kPreNone);  sink(slot, b, k, v).
-template <int LBMIN, int LBMAX, int NT, int PTS, bool SEQ_MINOR, int PRE, int ZS = 0, bool GSRC = false, class Src,
-          class Pre, class Sink>
-__device__ __forceinline__ void cg_fft(float2* __restrict__ Z, int LB, int nseq_log, const TwQ& tw, Src&& src,
+template <int LBMIN, int LBMAX, int NT, int PTS, bool SEQ_MINOR, int PRE, int ZS = 0, bool GSRC = false,
+          class TW, class Src, class Pre, class Sink>
+__device__ __forceinline__ void cg_fft(float2* __restrict__ Z, int LB, int nseq_log, const TW& tw, Src&& src,
                                        Pre&& pre, Sink&& sink) {
   const int P = (LB + 2) / 3;
   const int r0 = LB - 3 * (P - 1);  // radix bits of the first (remainder) pass

@@ -18,6 +18,8 @@
 //   k_fwd_cols2  the cols passes of two consecutive levels from one read of x.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "mrdft_fft.cuh"
 #include "mrdft_internal.h"
 
@@ -116,16 +118,25 @@ __device__ __forceinline__ void tile_chunk_levels_1_4(const FwdArgs& a, const fl
     st4s(B4 + pad16((chunk << 4) + 2 * q), make_float4(yr[2 * q].x, yr[2 * q].y, yr[2 * q + 1].x, yr[2 * q + 1].y));
 }
 
-template <int TLOG, int NT>
-__global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArgs a) {
+// LEAN: 3 CTAs per SM instead of 2 -- the odd-bin work area aliases the
+// level buffer (each thread reads the children of the bins it will store
+// before the FFT overwrites them), the twiddles come from the global table
+// through L1 instead of a shared copy, and registers are capped at 80.
+template <bool LEAN>
+constexpr size_t tile_smem() {
+  return (size_t)(kTile + pad16_size(kTile) + (LEAN ? 0 : kTile / 2 + twq_size(kTileLog))) * sizeof(float2) +
+         kMaxPack * sizeof(TileSig);
+}
+template <int TLOG, int NT, bool LEAN>
+__global__ void __launch_bounds__(NT, LEAN ? 3 : (NT <= 256 ? 2 : 1)) k_fwd_tile(const FwdArgs a) {
   constexpr int T = 1 << TLOG;
   static_assert(T == 16 * NT, "tile = 16 samples per thread");
   extern __shared__ __align__(1024) float2 sm[];
   float2* X = sm;                       // x tile (swz128)
   float2* B = sm + T;                   // current level, updated in place (pad16)
-  float2* Z = B + pad16_size(T);        // odd-bin DFT work area (zlay)
-  float2* TQ = Z + T / 2;               // quarter-wave w_{2^TLOG} (padded)
-  TileSig* TS = reinterpret_cast<TileSig*>(TQ + twq_size(TLOG));
+  float2* Z = LEAN ? B : B + pad16_size(T);  // odd-bin DFT work area (zlay)
+  float2* TQ = B + pad16_size(T) + T / 2;    // quarter-wave w_{2^TLOG} (padded; not LEAN)
+  TileSig* TS = reinterpret_cast<TileSig*>(LEAN ? B + pad16_size(T) : TQ + twq_size(TLOG));
   const int tid = threadIdx.x;
   const int item = blockIdx.x;
   if (item >= a.nitems) return;
@@ -162,10 +173,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
       const int e = c << 1;
       cp_async16(X + swz128(e), xg + TS[e >> tl].in_base + (e & ((1 << tl) - 1)));
     }
-    load_twq<NT>(TQ, TLOG, a.tw);
+    if constexpr (!LEAN) load_twq<NT>(TQ, TLOG, a.tw);
     cp_async_wait_all();
   } else {
-    load_twq<NT>(TQ, TLOG, a.tw);
+    if constexpr (!LEAN) load_twq<NT>(TQ, TLOG, a.tw);
 #pragma unroll 4
     for (int c = tid; c < (Tn >> 1); c += NT) {
       const int e = c << 1;
@@ -183,7 +194,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
 
   // ---- levels 5..tlog through the shared-memory FFT engine; B is updated in
   // place: every child read (pre) happens before the barrier in the last pass
-  const TwQ tw{TQ, TLOG};
+  // (LEAN: before the first pass's barrier, since Z is B)
+  using TWT = std::conditional_t<LEAN, TwG, TwQ>;
+  TWT tw;
+  if constexpr (LEAN) tw = TwG{a.tw.tw13, TLOG};
+  else tw = TwQ{TQ, TLOG};
   const bool single = it.nsig == 1;
   // one specialised FFT per level (compile-time lengths)
   static_for<5, TLOG + 1>([&](auto I) MRDFT_INL {
@@ -196,6 +211,20 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
     float2 ev[8];
     // V (Eq. 3) and D for a first-pass group: n = n0 + r 2^LRB, so
     // w_{2^i}^n = w_{2^i}^n0 w_{2R}^r with the second factor a constant
+    if constexpr (LEAN) {
+      // the children of this thread's last-pass bins (group G = tid of the
+      // last radix-8 pass: window G >> LRB, bins g + 2^LRB kk), read before
+      // the first pass writes the work area over them
+      constexpr int LRB = (i - 1) - 3;
+      if (tid < (Tn >> 4)) {
+        const int base = (tid >> LRB) << i, g = tid & ((1 << LRB) - 1);
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          const int k = g + (kk << LRB);
+          ev[kk] = cadd(B[pad16(base + k)], B[pad16(base + h + k)]);  // U: child sum
+        }
+      }
+    }
     auto src = [&](int b, int n0, int LRB, auto& v, auto RBc) MRDFT_INL {
       constexpr int R = 1 << decltype(RBc)::value;
       const int base = b << i;
@@ -207,8 +236,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
       });
     };
     auto pre = [&](int slot, int b, int k) MRDFT_INL {
-      const int base = b << i;
-      ev[slot] = cadd(B[pad16(base + k)], B[pad16(base + h + k)]);  // U: child sum
+      if constexpr (!LEAN) {
+        const int base = b << i;
+        ev[slot] = cadd(B[pad16(base + k)], B[pad16(base + h + k)]);  // U: child sum
+      }
     };
     auto sink = [&](int slot, int b, int k, float2 odd) MRDFT_INL {
       const int e = (b << i) + 2 * k;
@@ -224,7 +255,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_fwd_tile(const FwdArg
       if (l2keep) __stcg(dst, v);
       else __stcs(dst, v);
     };
-    cg_fft<i - 1, i - 1, NT, 8, false, true, 0, true>(Z, i - 1, tn_log - i, tw, src, pre, sink);
+    cg_fft<i - 1, i - 1, NT, 8, false, LEAN ? kPreNone : kPreBarrier, 0, true>(Z, i - 1, tn_log - i, tw, src, pre,
+                                                                                  sink);
     __syncthreads();
   });
 }
@@ -671,13 +703,15 @@ cudaError_t rows_attr() {
 
 // ================================================================ launchers
 
-static constexpr size_t kTileSmem =
-    (size_t)(kTile + pad16_size(kTile) + kTile / 2 + twq_size(kTileLog)) * sizeof(float2) + kMaxPack * sizeof(TileSig);
+
 static constexpr size_t kWinSmem = (size_t)((1 << kWinMaxLog) + twq_size(13)) * sizeof(float2);
 static_assert((1 << kWinMaxLog) % kWinThreads == 0, "points per thread");
 cudaError_t set_fwd_attributes() {
-  cudaError_t e = cudaFuncSetAttribute(k_fwd_tile<kTileLog, kTileThreads>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTileSmem);
+  cudaError_t e = cudaFuncSetAttribute(k_fwd_tile<kTileLog, kTileThreads, false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tile_smem<false>());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fwd_tile<kTileLog, kTileThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)tile_smem<true>());
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fwd_window<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmem);
   if (e == cudaSuccess)
@@ -704,7 +738,10 @@ cudaError_t set_fwd_attributes() {
 }
 
 cudaError_t launch_fwd_tile(const FwdArgs& a, int grid, cudaStream_t s) {
-  k_fwd_tile<kTileLog, kTileThreads><<<grid, kTileThreads, kTileSmem, s>>>(a);
+  if (a.tile_lean)
+    k_fwd_tile<kTileLog, kTileThreads, true><<<grid, kTileThreads, tile_smem<true>(), s>>>(a);
+  else
+    k_fwd_tile<kTileLog, kTileThreads, false><<<grid, kTileThreads, tile_smem<false>(), s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_tiny(const FwdArgs& a, int nsig_tiny, cudaStream_t s) {
@@ -749,6 +786,89 @@ cudaError_t launch_fwd_rows(const FwdArgs& a, int grid, cudaStream_t s) {
   static_for_host<9, 15>([&](auto C) {
     if (CB == decltype(C)::value) rows_launch<decltype(C)::value>(a, grid, s);
   });
+  return cudaGetLastError();
+}
+
+}  // namespace mrdft
+
+// ====================================================== bit-reversed layout
+//
+// MRDFT_FLAG_BITREV: each window of each level is rewritten in place in the
+// order of the paper's Sec. 3 before the permutation Gamma, i.e. position p of
+// a window of level i holds bin bitrev_i(p) (the matrix T_{2^i}, an
+// involution).  Runs after the natural-order forward.
+namespace mrdft {
+
+__device__ __forceinline__ uint32_t brev_bits(uint32_t v, int bits) { return bits ? __brev(v) >> (32 - bits) : 0; }
+
+// Levels i <= 12: a CTA takes one block of 2^B (B = min(m, 12)) outputs of
+// one level of one signal -- whole windows -- through shared memory.
+// Item: {sig, block, level}.
+__global__ void __launch_bounds__(256) k_bitrev_small(const FwdArgs a) {
+  __shared__ __align__(16) float2 buf[kTile];
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  if (it.sig < 0 || it.sig >= a.nsigs) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
+  const SigDesc sd = a.sigs[it.sig];
+  const int i = it.block;
+  const int B = sd.m < kTileLog ? sd.m : kTileLog;
+  if (i < 1 || i > B || it.window < 0 || ((int64_t)it.window << B) >= ((int64_t)1 << sd.m)) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
+  float2* base = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ((int64_t)it.window << B);
+  const int n = 1 << B;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) buf[e] = base[e];
+  __syncthreads();
+  const int mask = (1 << i) - 1;
+  for (int e = threadIdx.x; e < n; e += blockDim.x) base[e] = buf[(e & ~mask) | (int)brev_bits(e & mask, i)];
+}
+
+// Levels i > 12: window index k = hi (5 bits) | mid (i - 10 bits) | lo (5 bits);
+// bitrev(k) = rev(lo) | rev(mid) | rev(hi), so the 32 x 32 tile of a given mid
+// maps onto the tile of rev(mid), transposed with both coordinates reversed.
+// A CTA takes mid = M of one window (item {sig, window, level}, M =
+// blockIdx.y) and swaps tiles M and rev(M) (CTAs with M > rev(M) leave).
+__global__ void __launch_bounds__(256) k_bitrev_big(const FwdArgs a) {
+  __shared__ float2 ta[32][33], tb[32][33];
+  const LevelItem it = reinterpret_cast<const LevelItem*>(a.items)[blockIdx.x];
+  if (it.sig < 0 || it.sig >= a.nsigs) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
+  const SigDesc sd = a.sigs[it.sig];
+  const int i = it.block;
+  if (i <= kTileLog || i > sd.m || it.window < 0 || (int64_t)it.window >= ((int64_t)1 << (sd.m - i)) ||
+      (int)blockIdx.y >= (1 << (i - 10))) {
+    if (threadIdx.x == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
+  const uint32_t M = blockIdx.y, Mr = brev_bits(M, i - 10);
+  if (M > Mr) return;
+  float2* base = a.y + sd.out_off + ((int64_t)(i - 1) << sd.m) + ((int64_t)it.window << i);
+  auto addr = [&](uint32_t mid, int hi, int lo) { return base + (((int64_t)hi << (i - 5)) | ((int64_t)mid << 5) | lo); };
+  const int lo = threadIdx.x & 31, r0 = threadIdx.x >> 5;
+  for (int hi = r0; hi < 32; hi += 8) {
+    ta[hi][lo] = *addr(M, hi, lo);
+    tb[hi][lo] = *addr(Mr, hi, lo);
+  }
+  __syncthreads();
+  // tile Mr position (row R, col c) takes tile M element (hi = rev(c), lo = rev(R)); and vice versa
+  for (int R = r0; R < 32; R += 8) {
+    const int h = brev_bits(lo, 5), l = brev_bits(R, 5);
+    *addr(Mr, R, lo) = ta[h][l];
+    if (M != Mr) *addr(M, R, lo) = tb[h][l];
+  }
+}
+
+cudaError_t launch_bitrev_small(const FwdArgs& a, int grid, cudaStream_t s) {
+  k_bitrev_small<<<grid, 256, 0, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_bitrev_big(const FwdArgs& a, int grid, int level, cudaStream_t s) {
+  k_bitrev_big<<<dim3(grid, 1u << (level - 10)), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

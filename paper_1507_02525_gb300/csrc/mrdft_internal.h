@@ -78,6 +78,7 @@ struct FwdArgs {
   int cb_min;         // two-pass levels: C = 2^max(i - 12, cb_min), cb_min 9..11 (0 means 10)
   int rows14;         // C = 2^12 rows CTAs of 2^14 points (4 residues, 1 per SM) instead of 2^13
   int rows_pf;        // rows CTAs that copy the children into shared memory when they start
+  int tile_lean;      // tile CTAs in the 3-per-SM shape (work area aliasing the level buffer)
   Twiddles tw;
   int* status;
 };
@@ -151,6 +152,11 @@ cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_fwd_cols2(const FwdArgs& a, int grid, cudaStream_t s);
 bool fwd_cols2_pairable(int upper_level, int cb_min);
 cudaError_t launch_fwd_rows(const FwdArgs& a, int grid, cudaStream_t s);
+
+// bit-reversed output layout (MRDFT_FLAG_BITREV), in place after the forward:
+// items {sig, block, level} for levels <= 12, {sig, window, level} above
+cudaError_t launch_bitrev_small(const FwdArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_bitrev_big(const FwdArgs& a, int grid, int level, cudaStream_t s);
 
 cudaError_t launch_adj_tile(const AdjArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_adj_tiny(const AdjArgs& a, int nsig_tiny, cudaStream_t s);

@@ -127,10 +127,17 @@ struct mrdft_plan_s {
   int n_tiny = 0;
   LevelItem* d_levels = nullptr;
   int64_t n_level_items = 0;
+  // MRDFT_FLAG_BITREV: items of the in-place permutation after the forward
+  LevelItem* d_br = nullptr;
+  int br_small = 0;                                   // {sig, block, level}, levels 2..12
+  std::vector<std::pair<int, std::pair<int64_t, int>>> br_big;  // level, (first item, count), levels > 12
   std::vector<Segment> segments;
   std::vector<Launch> top;  // levels above seg_log, ascending, whole plan (adjoint; forward without the tree)
   std::vector<TopNode> top_nodes;   // forward tree (children before parents)
-  bool fwd_tree = true;             // off: the forward runs `top` after every segment instead
+  bool fwd_tree = false;            // off: the forward runs `top` after every segment instead
+  bool tile_first = false;          // one tile launch over every segment (before them forward, after them adjoint)
+  bool tile_lean = false;           // forward tile CTAs in the 3-per-SM shape
+  Launch tile_all{};                // that launch (tile_first)
   std::vector<cudaEvent_t> ev_seg, ev_node;
   int seg_log = 23;
   int nstreams = 4;
@@ -142,7 +149,7 @@ struct mrdft_plan_s {
   int adj_cb_min = 10;         // adjoint two-pass levels: C = 2^max(i - 12, adj_cb_min)
   int fwd_rows14 = 1;          // forward C = 2^12 rows CTAs of 2^14 points (else 2^13; last-pass children reads only)
   int fwd_cb_min = 9;          // forward two-pass levels: C = 2^max(i - 12, fwd_cb_min)
-  int fwd_rows_pf = 1;         // forward rows CTAs prefetch the children into shared memory
+  int fwd_rows_pf = 0;         // forward rows CTAs prefetch the children into shared memory
   std::vector<cudaStream_t> workers;
   std::vector<cudaEvent_t> ev_join;
   cudaEvent_t ev_fork = nullptr;
@@ -283,7 +290,7 @@ void release(mrdft_plan_s* p) {
   for (auto& g : p->adj_graphs) cudaGraphExecDestroy(g.exec);
   p->fwd_graphs.clear();
   p->adj_graphs.clear();
-  void* ptrs[] = {p->d_sigs, p->d_tile_ids, p->d_tiles, p->d_tiny_ids, p->d_levels,
+  void* ptrs[] = {p->d_sigs, p->d_tile_ids, p->d_tiles, p->d_tiny_ids, p->d_levels, p->d_br,
                   p->d_tw13, p->d_twlo, p->d_twhi, p->d_scratch, p->d_e0,
                   p->d_e1, p->d_etop, p->d_acc, p->d_status, p->d_stage_x, p->d_stage_y};
   for (void* q : ptrs)
@@ -436,7 +443,12 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
       T.bytes += ((int64_t)n << m) * (in_b + 8 * m);
     }
     T.count = (int)((int64_t)tiles.size() - T.off);
-    if (T.count) seg.chain.push_back(T);
+    if (T.count) {
+      // segments append their tile items one after another: with tile_first
+      // the union [0, tiles) is one launch
+      if (p->tile_first) p->tile_all.bytes += T.bytes;
+      else seg.chain.push_back(T);
+    }
     // levels above the tile, inside the segment
     for (int i = kTileLog + 1; i <= S; ++i) {
       Launch L{};
@@ -477,6 +489,11 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     if (L.count) p->top.push_back(L);
   }
   pair_levels(p->top);
+  if (p->tile_first) {
+    p->tile_all.kind = LK_TILE;
+    p->tile_all.off = 0;
+    p->tile_all.count = (int)tiles.size();
+  }
   if (p->fwd_tree && !p->top.empty()) {
     // segment of each (signal, level-S window) of the signals longer than a segment
     std::map<std::pair<int32_t, int32_t>, int> seg_of;
@@ -513,6 +530,23 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
   p->n_tiles = (int)tiles.size();
   p->n_tile_ids = (int)tile_ids.size();
   p->n_level_items = (int64_t)litems.size();
+  std::vector<LevelItem> br;
+  if (p->flags & MRDFT_FLAG_BITREV) {
+    for (int64_t sg = 0; sg < batch; ++sg) {
+      const int m = p->sigs[sg].m, B = std::min(m, kTileLog);
+      for (int i = 2; i <= B; ++i)
+        for (int64_t b = 0; b < (int64_t(1) << (m - B)); ++b) br.push_back(LevelItem{(int32_t)sg, (int32_t)b, i, 0});
+    }
+    p->br_small = (int)br.size();
+    for (int i = kTileLog + 1; i <= p->max_m; ++i) {
+      const int64_t first = (int64_t)br.size();
+      for (int64_t sg = 0; sg < batch; ++sg)
+        if (p->sigs[sg].m >= i)
+          for (int64_t w = 0; w < (int64_t(1) << (p->sigs[sg].m - i)); ++w)
+            br.push_back(LevelItem{(int32_t)sg, (int32_t)w, i, 0});
+      p->br_big.push_back({i, {first, (int)((int64_t)br.size() - first)}});
+    }
+  }
   p->n_tiny = (int)tiny_ids.size();
 
   // streams and events for the concurrent segment chains
@@ -548,6 +582,7 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
   MRDFT_CUDA(p, dev_upload(&p->d_tiles, tiles));
   MRDFT_CUDA(p, dev_upload(&p->d_tiny_ids, tiny_ids));
   MRDFT_CUDA(p, dev_upload(&p->d_levels, litems));
+  MRDFT_CUDA(p, dev_upload(&p->d_br, br));
   MRDFT_CUDA(p, dev_upload(&p->d_tw13, tw13));
   MRDFT_CUDA(p, dev_upload(&p->d_twlo, twlo));
   MRDFT_CUDA(p, dev_upload(&p->d_twhi, twhi));
@@ -649,6 +684,7 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
   a.cb_min = p->fwd_cb_min;
   a.rows14 = p->fwd_rows14;
   a.rows_pf = p->fwd_rows_pf;
+  a.tile_lean = p->tile_lean;
   a.tw = twiddles(p);
   a.status = p->d_status;
   if (p->n_tiny) {
@@ -657,6 +693,10 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
     t.nids = p->n_tiny;
     t.nitems = p->n_tiny;
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_TINY, 0, st, [&] { return launch_fwd_tiny(t, p->n_tiny, st); }));
+  }
+  if (p->tile_first && p->tile_all.count) {
+    mrdft_status q = launch_fwd(p, a, p->tile_all, st);
+    if (q != MRDFT_OK) return q;
   }
   const bool tree = !p->top_nodes.empty();
   // forward tree: a node is enqueued right after the later of its two
@@ -697,10 +737,25 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
         return child_done(p->segments[j].parent, s);
       });
   if (r != MRDFT_OK) return r;
-  if (tree) return MRDFT_OK;
-  for (const Launch& L : p->top) {
-    r = launch_fwd(p, a, L, st);
-    if (r != MRDFT_OK) return r;
+  if (!tree) {
+    for (const Launch& L : p->top) {
+      r = launch_fwd(p, a, L, st);
+      if (r != MRDFT_OK) return r;
+    }
+  }
+  if (p->flags & MRDFT_FLAG_BITREV) {
+    // every window rewritten in place in the bit-reversed order of Sec. 3
+    FwdArgs b = a;
+    if (p->br_small) {
+      b.items = p->d_br;
+      b.nitems = p->br_small;
+      MRDFT_CUDA(p, launch_bitrev_small(b, p->br_small, st));
+    }
+    for (const auto& lv : p->br_big) {
+      b.items = p->d_br + lv.second.first;
+      b.nitems = lv.second.second;
+      MRDFT_CUDA(p, launch_bitrev_big(b, lv.second.second, lv.first, st));
+    }
   }
   return MRDFT_OK;
 }
@@ -778,6 +833,10 @@ mrdft_status enqueue_adjoint(mrdft_plan_s* p, const void* gy, void* gx, cudaStre
     return MRDFT_OK;
   });
   if (r != MRDFT_OK) return r;
+  if (p->tile_first && p->tile_all.count) {
+    r = launch_adj(p, a, p->tile_all, st, false);
+    if (r != MRDFT_OK) return r;
+  }
   if (p->n_tiny) {
     AdjArgs t = a;
     t.sig_ids = p->d_tiny_ids;
@@ -885,7 +944,8 @@ mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: fwd_cb must be 0 or in [9, 11]");
   if (o.adj_cb != 0 && (o.adj_cb < 9 || o.adj_cb > 10))
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: adj_cb must be 0 or in [9, 10]");
-  if (!sw(o.fwd_rows_prefetch) || !sw(o.fwd_rows14) || !sw(o.adj_rows13) || !sw(o.dual_cols) || !sw(o.fwd_tree))
+  if (!sw(o.fwd_rows_prefetch) || !sw(o.fwd_rows14) || !sw(o.adj_rows13) || !sw(o.dual_cols) || !sw(o.fwd_tree) ||
+      !sw(o.tile_first) || !sw(o.tile_lean))
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: switches must be MRDFT_OPT_DEFAULT, _OFF or _ON");
   if (!lengths) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: lengths is NULL");
   if (batch < 1 || batch > (int64_t(1) << 30))
@@ -893,7 +953,7 @@ mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_
   if (n_lengths != 1 && n_lengths != batch)
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: n_lengths must be 1 or batch");
   if (dtype != MRDFT_C64 && dtype != MRDFT_R32) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: unknown dtype");
-  if (flags & ~MRDFT_FLAG_GRAPH) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: unknown flag bits");
+  if (flags & ~(MRDFT_FLAG_GRAPH | MRDFT_FLAG_BITREV)) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: unknown flag bits");
   int64_t total = 0;
   for (int64_t s = 0; s < n_lengths; ++s) {
     const int64_t N = lengths[s];
@@ -923,6 +983,8 @@ mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_
   p->adj_rows13 = on(o.adj_rows13, p->adj_rows13 != 0);
   p->dual_cols = on(o.dual_cols, p->dual_cols);
   p->fwd_tree = on(o.fwd_tree, p->fwd_tree);
+  p->tile_first = on(o.tile_first, p->tile_first);
+  p->tile_lean = on(o.tile_lean, p->tile_lean);
   mrdft_status st = build_plan(p, lengths, n_lengths, batch);
   if (st != MRDFT_OK) {
     fail(nullptr, st, p->err);
@@ -946,6 +1008,8 @@ mrdft_status mrdft_plan_get_opts(mrdft_plan_t p, mrdft_exec_opts* opts) {
   opts->adj_rows13 = sw(p->adj_rows13 != 0);
   opts->dual_cols = sw(p->dual_cols);
   opts->fwd_tree = sw(p->fwd_tree);
+  opts->tile_first = sw(p->tile_first);
+  opts->tile_lean = sw(p->tile_lean);
   return MRDFT_OK;
 }
 
@@ -972,6 +1036,8 @@ mrdft_status mrdft_adjoint(mrdft_plan_t p, const void* gy, void* gx, mrdft_strea
   if (!p) return fail(nullptr, MRDFT_EINVAL, "mrdft_adjoint: plan is NULL");
   if (!gy || !gx) return fail(p, MRDFT_EINVAL, "mrdft_adjoint: gy or gx is NULL");
   if (misaligned(gy) || misaligned(gx)) return fail(p, MRDFT_EINVAL, "mrdft_adjoint: gy and gx must be 16-byte aligned");
+  if (p->flags & MRDFT_FLAG_BITREV)
+    return fail(p, MRDFT_EUNSUPPORTED, "mrdft_adjoint: plans with MRDFT_FLAG_BITREV are forward-only");
   return run(p, p->adj_graphs, enqueue_adjoint, gy, gx, reinterpret_cast<cudaStream_t>(stream));
 }
 
@@ -983,6 +1049,8 @@ mrdft_status mrdft_loss_grad(mrdft_plan_t p, const void* x, const void* t, void*
     return fail(p, MRDFT_EINVAL, "mrdft_loss_grad: buffers must be 16-byte aligned");
   if (loss && (reinterpret_cast<uintptr_t>(loss) & 7) != 0)
     return fail(p, MRDFT_EINVAL, "mrdft_loss_grad: loss must be 8-byte aligned");
+  if (p->flags & MRDFT_FLAG_BITREV)
+    return fail(p, MRDFT_EUNSUPPORTED, "mrdft_loss_grad: plans with MRDFT_FLAG_BITREV are forward-only");
   cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
   mrdft_status s = run(p, p->fwd_graphs, enqueue_forward, x, y, st);
   if (s != MRDFT_OK) return s;
@@ -1047,6 +1115,7 @@ mrdft_status mrdft_plan_info(mrdft_plan_t p, int32_t* tile_log, int32_t* fwd_lau
   };
   for (const Segment& g : p->segments)
     for (const Launch& L : g.chain) count(L);
+  if (p->tile_first && p->tile_all.count) count(p->tile_all);
   if (p->top_nodes.empty()) {
     for (const Launch& L : p->top) count(L);
   } else {

@@ -96,14 +96,14 @@ def test_tune_plan_searches_kernel_variants(tmp_path, monkeypatch):
         ms = abs(o["seg_log"] - 21) + 0.1 * o["streams"] + 5.0
         ms -= 0.5 if o.get("fwd_cb") == 10 else 0.0       # clearly faster: kept
         ms -= 0.001 if o.get("dual_cols") is False else 0.0  # within the margin: not kept
-        ms -= 0.3 if o.get("fwd_tree") is False else 0.0
+        ms -= 0.3 if o.get("fwd_tree") is True else 0.0
         return ms
 
     best = autotune.tune_plan([1 << 24], 1, objective="forward", timer=timer,
                               candidates=[(20, 4), (21, 2), (22, 4)])
-    assert best == {"seg_log": 21, "streams": 2, "fwd_cb": 10, "fwd_tree": False}
+    assert best == {"seg_log": 21, "streams": 2, "fwd_cb": 10, "fwd_tree": True}
     names = {k for o in seen for k in o}
-    assert {"fwd_cb", "fwd_rows_prefetch", "dual_cols", "fwd_tree"} <= names
+    assert {"fwd_cb", "fwd_rows_prefetch", "dual_cols", "fwd_tree", "tile_first"} <= names
     assert not any("adj_cb" in o for o in seen)
     n = len(seen)
     assert autotune.tune_plan([1 << 24], 1, objective="forward", timer=lambda o: 1 / 0) == best

@@ -750,3 +750,92 @@ def test_autotuned_plan(oracle, tmp_path, monkeypatch):
     for s in (0, 7):
         check_forward_levels(yn[s], oracle.forward(x[s].astype(np.complex128)), x[s], f"signal {s}")
     plan.close()
+
+
+# ------------------------------------------------- bit-reversed output layout
+
+def _bitrev_perm(i):
+    k = np.arange(1 << i)
+    r = np.zeros_like(k)
+    for b in range(i):
+        r |= ((k >> b) & 1) << (i - 1 - b)
+    return r
+
+
+def test_bitrev_permutation_is_the_papers_T():
+    """The permutation the bit-reversed layout applies to a window of level i is
+    the matrix T_{2^i} of Sec. 3 (built from its definition in oracle.matrices,
+    itself pinned by the printed T_4 and T_8)."""
+    from oracle import matrices
+    for i in range(1, 7):
+        v = np.arange(1 << i) + 1j * np.arange(1 << i)[::-1]
+        np.testing.assert_array_equal(matrices.T(i) @ v, v[_bitrev_perm(i)])
+
+
+@pytest.mark.parametrize("lengths", [[1 << 10], [1 << 16] * 3, [1 << 24],
+                                     [1 << k for k in (3, 9, 13, 15, 12, 17, 4, 14, 20, 1)]])
+def test_forward_bitrev_layout(oracle, lengths):
+    """MRDFT_FLAG_BITREV: every window of every level holds the oracle's bins in
+    the bit-reversed order T_{2^i} of Sec. 3 (tiny, in-tile, window and
+    two-pass levels, a 2^24 signal, ragged lengths), and the same plan with
+    graph replay gives the same bits; the adjoint is refused."""
+    x = inputs.complex_signals(1, sum(lengths), seed=202)[0]
+    plan = _lib.Plan(lengths, len(lengths), bitrev=True)
+    y = run_forward(plan, x)
+    gplan = _lib.Plan(lengths, len(lengths), bitrev=True, graph=True)
+    xt = torch.from_numpy(x).cuda()
+    yg = torch.empty(gplan.out_elems, dtype=torch.complex64, device="cuda")
+    for _ in range(2):
+        gplan.forward(xt.data_ptr(), yg.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(yg.cpu().numpy(), y)
+    ys = split_out(y, lengths)
+    for s, (xs, ys_) in enumerate(zip(split_in(x, lengths), ys)):
+        m = ys_.shape[0]
+        x128 = xs.astype(np.complex128)
+        ref = oracle.forward(x128) if m <= 20 else None
+        for i in range(1, m + 1):
+            nat = ref[i - 1] if ref is not None else oracle.forward_level(x128, i)
+            want = nat.reshape(-1, 1 << i)[:, _bitrev_perm(i)].reshape(-1)
+            d = ys_[i - 1].astype(np.complex128) - want
+            assert np.linalg.norm(d) <= 2e-6 * i * np.linalg.norm(want), f"s={s} level {i}"
+    with pytest.raises(_lib.MrdftError) as e:
+        plan.adjoint(xt.data_ptr(), xt.data_ptr(), 0)
+    assert e.value.status == _lib.MRDFT_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("seg_log", [12, 14, 17, 23])
+def test_tile_first_both_directions(oracle, seg_log):
+    """tile_first: the in-tile levels of every segment as one launch, ahead of
+    the segments in the forward and after them in the adjoint (which then reads
+    every segment's accumulator and level-13 propagation at the end)."""
+    lengths = [1 << 18, 1 << 12, 1 << 16, 1 << 9, 1 << 15, 1 << 13]
+    x = inputs.complex_signals(1, sum(lengths), seed=404)[0]
+    plan = _lib.Plan(lengths, len(lengths), seg_log=seg_log, streams=3, opts={"tile_first": True})
+    assert plan.opts()["tile_first"] is True
+    ys = split_out(run_forward(plan, x), lengths)
+    gy = inputs.complex_signals(1, plan.out_elems, seed=405)[0]
+    gx = split_in(run_adjoint(plan, gy), lengths)
+    gys = split_out(gy, lengths)
+    for s, xs in enumerate(split_in(x, lengths)):
+        check_forward_levels(ys[s], oracle.forward(xs.astype(np.complex128)), xs, f"S={seg_log} s={s}")
+        check_adjoint(gx[s], oracle.adjoint(gys[s].astype(np.complex128)), gys[s], f"S={seg_log} s={s}")
+
+
+@pytest.mark.parametrize("real", [False, True])
+def test_tile_lean_forward(oracle, real):
+    """tile_lean: the forward tile CTAs that fit three to an SM (work area
+    sharing the level buffer, twiddles through L1): every length from 2^5 to
+    2^16, packed tiles of short signals, ragged, real and complex input."""
+    rng = np.random.default_rng(505)
+    ks = list(range(5, 17)) + list(rng.integers(5, 13, size=40)) + [12] * 5 + [6] * 70
+    rng.shuffle(ks)
+    lengths = [1 << int(k) for k in ks]
+    total = sum(lengths)
+    x = (inputs.real_signals(1, total, seed=506)[0] if real
+         else inputs.complex_signals(1, total, seed=506)[0])
+    plan = _lib.Plan(lengths, len(lengths), real_input=real, opts={"tile_lean": True})
+    assert plan.opts()["tile_lean"] is True
+    ys = split_out(run_forward(plan, x), lengths)
+    for s, xs in enumerate(split_in(x, lengths)):
+        check_forward_levels(ys[s], oracle.forward(xs.astype(np.complex128)), xs, f"lean s={s} N={len(xs)}")
