@@ -113,6 +113,13 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def traffic_key(workload: str, opts: dict) -> str:
+    """Key of a plan's DRAM-traffic record: the workload, segment size x
+    streams, and a digest of every execution option."""
+    dig = hashlib.sha1(json.dumps(opts, sort_keys=True).encode()).hexdigest()[:8]
+    return f"{workload}:seg{opts.get('seg_log')}x{opts.get('streams')}:{dig}"
+
+
 def ncu_traffic(kernel: str, workload: str):
     """DRAM bytes per launch of `kernel` from profiles/ncu_traffic.txt, only if the
     recorded source hash matches the kernels built now (else None)."""
@@ -340,6 +347,11 @@ def main():
     ap.add_argument("--no-train", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-others", action="store_true", help="skip the other workloads' extra keys")
+    ap.add_argument("--profile-run", default=None, choices=["fwd", "adj"],
+                    help="profiling mode: plan the workload with --opts (JSON execution options, else the "
+                         "library defaults), run --warmup + --steps calls in that direction and exit; prints "
+                         "the kernel launches of one call (for ncu -s / -c)")
+    ap.add_argument("--opts", default=None, help="execution options (JSON) for --profile-run")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -377,6 +389,29 @@ def main():
 
     import torch
     from paper_1507_02525_gb300 import _lib, replicas
+
+    if args.profile_run:
+        opts = json.loads(args.opts) if args.opts else {}
+        plan = _lib.Plan(lengths, len(lengths), real_input=real_input, opts=opts)
+        x_np = make_input(args.workload)
+        xt = torch.from_numpy(x_np).cuda()
+        y = torch.empty(plan.out_elems, dtype=torch.complex64, device="cuda")
+        gx = torch.empty(plan.in_elems, dtype=torch.complex64, device="cuda")
+        sp = torch.cuda.current_stream().cuda_stream
+        if args.profile_run == "adj":
+            plan.forward(xt.data_ptr(), y.data_ptr(), sp)
+        for _ in range(args.warmup + args.steps):
+            if args.profile_run == "fwd":
+                plan.forward(xt.data_ptr(), y.data_ptr(), sp)
+            else:
+                plan.adjoint(y.data_ptr(), gx.data_ptr(), sp)
+        torch.cuda.synchronize()
+        plan.status_poll()
+        info = plan.info()
+        print(json.dumps({"profile_run": args.profile_run, "workload": args.workload, "opts": plan.opts(),
+                          "launches_per_call": info["fwd_launches" if args.profile_run == "fwd" else "adj_launches"],
+                          "launches_before_timed": (1 if args.profile_run == "adj" else 0) * info["fwd_launches"]}))
+        return 0
 
     if world > 1:
         import torch.distributed as dist
@@ -455,20 +490,24 @@ def main():
 
     # per-kernel device time: events around each launch, launches serialised
     # on the bench stream so that each bracketed kernel has the GPU to itself,
-    # on a plan of the same workload without segments (one launch per level
-    # over whole signals: the full-size launches the roofline is about)
-    kplan = _lib.Plan(lengths, len(lengths), real_input=real_input, graph=False, seg_log=26, streams=1)
-    kplan.timing_enable(True, serial=True)
-    for _ in range(2):
-        kplan.forward(xt.data_ptr(), y.data_ptr(), sp)
-    kf = kplan.timing_read()
-    kplan.timing_enable(True, serial=True)
-    for _ in range(2):
-        kplan.adjoint(y.data_ptr(), gx.data_ptr(), sp)
-    ka = kplan.timing_read()
-    kplan.timing_enable(False)
-    kplan.status_poll()
-    kplan.close()
+    # on plans with the timed plans' own execution options (the same
+    # segments, launches and work lists as the timed steps)
+    def kernel_times(opts, direction):
+        kp = _lib.Plan(lengths, len(lengths), real_input=real_input, graph=False, opts=opts)
+        kp.timing_enable(True, serial=True)
+        for _ in range(2):
+            if direction == "fwd":
+                kp.forward(xt.data_ptr(), y.data_ptr(), sp)
+            else:
+                kp.adjoint(y.data_ptr(), gx.data_ptr(), sp)
+        kt = kp.timing_read()
+        kp.timing_enable(False)
+        kp.status_poll()
+        kp.close()
+        return kt
+
+    kf = kernel_times(plan.opts(), "fwd")
+    ka = kernel_times(plan_adj.opts(), "adj")
 
     peak, peak_src = measured_peaks()
 
@@ -476,7 +515,7 @@ def main():
     # intermediate (no algorithmic bytes), the rows launch writes the level
     partner = {"fwd_cols": "fwd_rows", "adj_cols": "adj_rows"}
 
-    def dominant(kt, total_ms_per_step):
+    def dominant(kt, total_ms_per_step, opts):
         units = {}
         for k, (ms, n, b) in kt.items():
             if k in partner:
@@ -494,7 +533,7 @@ def main():
         # over the part's launches and spread over the unit's launches (a
         # dual-level cols launch serves two rows launches)
         traffic = None
-        tr = [ncu_traffic(q, args.workload + "_noseg") for q in parts]
+        tr = [ncu_traffic(q, traffic_key(args.workload, opts)) for q in parts]
         if all(t is not None for t in tr):
             traffic = int(sum(t * kt[q][1] for t, q in zip(tr, parts)) / n)
         share = ms / sum(v[0] for v in kt.values())
@@ -503,12 +542,13 @@ def main():
                 "alg_bytes_per_launch": int(bytes_per_launch), "ms_per_launch": round(per_launch_ms, 4),
                 "share_of_kernel_time": round(share, 3), "peak_source": peak_src,
                 "timing": ("CUDA events around every launch on the bench stream, launches serialised, "
-                           "2 steps of the same workload planned without segments (one launch per level)"),
+                           "2 steps of the timed plan's own execution options"),
+                "traffic_key": traffic_key(args.workload, opts),
                 "per_kernel_ms_per_step": {k: round(v[0] / 2, 4) for k, v in kt.items()},
                 "per_kernel_gbs": {k: round(v[2] / (v[0] * 1e-3) / 1e9, 1) for k, v in kt.items() if v[2]}}
 
-    roof_fwd = dominant(kf, ms_fwd)
-    roof_adj = dominant(ka, ms_adj)
+    roof_fwd = dominant(kf, ms_fwd, plan.opts())
+    roof_adj = dominant(ka, ms_adj, plan_adj.opts())
     total_samples = replicas.sum_over_ranks(nsamp, device=dev)
     value = replicas.job_throughput(total_samples, ms_fwd) / 1e9
     value_adj = replicas.job_throughput(total_samples, ms_adj) / 1e9

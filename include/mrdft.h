@@ -128,10 +128,10 @@ mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t 
  *              those levels run level by level after every segment
  *   tile_first : the in-tile levels of every segment run as one launch,
  *              before the segments (forward) or after them (adjoint),
- *              instead of one launch per segment (default off)
+ *              instead of one launch per segment (default on)
  *   tile_lean : forward tile CTAs that fit three to an SM (the FFT work
  *              area shares the level buffer, twiddles read through L1)
- *              instead of two (default off)
+ *              instead of two (default on)
  */
 #define MRDFT_OPT_DEFAULT 0
 #define MRDFT_OPT_OFF 1

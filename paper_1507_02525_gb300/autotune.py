@@ -34,9 +34,9 @@ OBJECTIVES = ("both", "forward", "adjoint")
 # kernel variants searched after the shape, per objective: (option, values);
 # the first value of each is the library default
 FWD_KNOBS = (("fwd_cb", (9, 10, 11)), ("fwd_rows_prefetch", (False, True)), ("dual_cols", (True, False)),
-             ("fwd_tree", (False, True)), ("tile_first", (False, True)))
+             ("fwd_tree", (False, True)), ("tile_first", (True, False)))
 ADJ_KNOBS = (("adj_cb", (10, 9)), ("adj_rows13", (True, False)), ("dual_cols", (True, False)),
-             ("tile_first", (False, True)))
+             ("tile_first", (True, False)))
 KEEP_MARGIN = 0.99  # a variant replaces the current choice only when at least 1% faster
 
 

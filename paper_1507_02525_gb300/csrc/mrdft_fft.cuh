@@ -81,6 +81,24 @@ __device__ __forceinline__ float2 twq(const TwG& t, int e) {
 }
 __device__ __forceinline__ float2 twq_l(const TwG& t, int l, int e) { return twq(t, e << (t.TB - l)); }
 
+// A two-level table in shared memory: w_{2^TB}^e = hi[e >> 6] lo[e & 63]
+// (hi[j] = w^(64 j), lo[k] = w^k, both FP64 values rounded once; one extra
+// rounding in the product), 2^(TB-6) + 64 entries -- 1 KB for TB = 12 instead
+// of the quarter-wave table's 8.7 KB.  Entries are padded (k + k / 16) so that
+// lanes reading exponents with a power-of-two stride hit distinct banks.
+struct TwS {
+  const float2* hi;
+  const float2* lo;
+  int TB;
+};
+__host__ __device__ constexpr int tws_size(int TB) { return (1 << (TB - 6)) + ((1 << (TB - 6)) >> 4) + 64 + 4; }
+__device__ __forceinline__ int tws_pad(int k) { return k + (k >> 4); }
+__device__ __forceinline__ float2 twq(const TwS& t, int e) {
+  e &= (1 << t.TB) - 1;
+  return cmul(t.hi[tws_pad(e >> 6)], t.lo[tws_pad(e & 63)]);
+}
+__device__ __forceinline__ float2 twq_l(const TwS& t, int l, int e) { return twq(t, e << (t.TB - l)); }
+
 // w^(k * step), k = 0 .. R-1, from one table entry (w^step) and products of
 // it (at most four extra roundings, far inside the FP32 error budget): one
 // lookup instead of log2(R) keeps the table-index and quadrant arithmetic off
@@ -259,6 +277,19 @@ template <int NT>
 __device__ __forceinline__ void load_twq(float2* q, int TB, const Twiddles& T) {
   const int n = 1 << (TB - 2);
   for (int r = threadIdx.x; r < n; r += NT) q[twq_pad(r)] = __ldg(&T.tw13[r << (kTwLog - TB)]);
+}
+
+// Fill a two-level table (TwS) of w_{2^TB} at q: hi first, then lo.
+template <int NT>
+__device__ __forceinline__ TwS load_tws(float2* q, int TB, const Twiddles& T) {
+  const int nh = 1 << (TB - 6);
+  float2* hi = q;
+  float2* lo = q + tws_pad(nh - 1) + 1;
+  for (int r = threadIdx.x; r < nh + 64; r += NT) {
+    if (r < nh) hi[tws_pad(r)] = __ldg(&T.tw13[(r << 6) << (kTwLog - TB)]);
+    else lo[tws_pad(r - nh)] = __ldg(&T.tw13[(r - nh) << (kTwLog - TB)]);
+  }
+  return TwS{hi, lo, TB};
 }
 
 // no-op pre-sink

@@ -120,11 +120,12 @@ __device__ __forceinline__ void tile_chunk_levels_1_4(const FwdArgs& a, const fl
 
 // LEAN: 3 CTAs per SM instead of 2 -- the odd-bin work area aliases the
 // level buffer (each thread reads the children of the bins it will store
-// before the FFT overwrites them), the twiddles come from the global table
-// through L1 instead of a shared copy, and registers are capped at 80.
+// before the FFT overwrites them), the twiddles come from a 1 KB two-level
+// table (TwS) instead of the quarter-wave one, and registers are capped at 80.
 template <bool LEAN>
 constexpr size_t tile_smem() {
-  return (size_t)(kTile + pad16_size(kTile) + (LEAN ? 0 : kTile / 2 + twq_size(kTileLog))) * sizeof(float2) +
+  return (size_t)(kTile + pad16_size(kTile) + (LEAN ? tws_size(kTileLog) : kTile / 2 + twq_size(kTileLog))) *
+             sizeof(float2) +
          kMaxPack * sizeof(TileSig);
 }
 template <int TLOG, int NT, bool LEAN>
@@ -135,8 +136,8 @@ __global__ void __launch_bounds__(NT, LEAN ? 3 : (NT <= 256 ? 2 : 1)) k_fwd_tile
   float2* X = sm;                       // x tile (swz128)
   float2* B = sm + T;                   // current level, updated in place (pad16)
   float2* Z = LEAN ? B : B + pad16_size(T);  // odd-bin DFT work area (zlay)
-  float2* TQ = B + pad16_size(T) + T / 2;    // quarter-wave w_{2^TLOG} (padded; not LEAN)
-  TileSig* TS = reinterpret_cast<TileSig*>(LEAN ? B + pad16_size(T) : TQ + twq_size(TLOG));
+  float2* TQ = LEAN ? B + pad16_size(T) : B + pad16_size(T) + T / 2;  // twiddle table (LEAN: two-level)
+  TileSig* TS = reinterpret_cast<TileSig*>(TQ + (LEAN ? tws_size(TLOG) : twq_size(TLOG)));
   const int tid = threadIdx.x;
   const int item = blockIdx.x;
   if (item >= a.nitems) return;
@@ -174,9 +175,11 @@ __global__ void __launch_bounds__(NT, LEAN ? 3 : (NT <= 256 ? 2 : 1)) k_fwd_tile
       cp_async16(X + swz128(e), xg + TS[e >> tl].in_base + (e & ((1 << tl) - 1)));
     }
     if constexpr (!LEAN) load_twq<NT>(TQ, TLOG, a.tw);
+    else load_tws<NT>(TQ, TLOG, a.tw);
     cp_async_wait_all();
   } else {
     if constexpr (!LEAN) load_twq<NT>(TQ, TLOG, a.tw);
+    else load_tws<NT>(TQ, TLOG, a.tw);
 #pragma unroll 4
     for (int c = tid; c < (Tn >> 1); c += NT) {
       const int e = c << 1;
@@ -195,9 +198,9 @@ __global__ void __launch_bounds__(NT, LEAN ? 3 : (NT <= 256 ? 2 : 1)) k_fwd_tile
   // ---- levels 5..tlog through the shared-memory FFT engine; B is updated in
   // place: every child read (pre) happens before the barrier in the last pass
   // (LEAN: before the first pass's barrier, since Z is B)
-  using TWT = std::conditional_t<LEAN, TwG, TwQ>;
+  using TWT = std::conditional_t<LEAN, TwS, TwQ>;
   TWT tw;
-  if constexpr (LEAN) tw = TwG{a.tw.tw13, TLOG};
+  if constexpr (LEAN) tw = TwS{TQ, TQ + tws_pad((1 << (TLOG - 6)) - 1) + 1, TLOG};
   else tw = TwQ{TQ, TLOG};
   const bool single = it.nsig == 1;
   // one specialised FFT per level (compile-time lengths)

@@ -135,8 +135,8 @@ struct mrdft_plan_s {
   std::vector<Launch> top;  // levels above seg_log, ascending, whole plan (adjoint; forward without the tree)
   std::vector<TopNode> top_nodes;   // forward tree (children before parents)
   bool fwd_tree = false;            // off: the forward runs `top` after every segment instead
-  bool tile_first = false;          // one tile launch over every segment (before them forward, after them adjoint)
-  bool tile_lean = false;           // forward tile CTAs in the 3-per-SM shape
+  bool tile_first = true;           // one tile launch over every segment (before them forward, after them adjoint)
+  bool tile_lean = true;            // forward tile CTAs in the 3-per-SM shape
   Launch tile_all{};                // that launch (tile_first)
   std::vector<cudaEvent_t> ev_seg, ev_node;
   int seg_log = 23;
