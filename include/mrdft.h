@@ -132,6 +132,13 @@ mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t 
  *   tile_lean : forward tile CTAs that fit three to an SM (the FFT work
  *              area shares the level buffer, twiddles read through L1)
  *              instead of two (default on)
+ *   fwd_rows12 : forward C = 2^9 rows CTAs of 2^12 points (256 threads, up
+ *              to four per SM) instead of 2^13 (512 threads) (default off)
+ *   tile_split : with tile_first, the in-tile levels run as this many launches
+ *              over consecutive groups of segments, 1..64 (default 1): each
+ *              group's segments start (forward) as soon as its own tiles are
+ *              done, while the next group's tiles run; in the adjoint a
+ *              group's tiles start as soon as its segments are done
  */
 #define MRDFT_OPT_DEFAULT 0
 #define MRDFT_OPT_OFF 1
@@ -148,6 +155,8 @@ typedef struct {
   int32_t fwd_tree;
   int32_t tile_first;
   int32_t tile_lean;
+  int32_t fwd_rows12;
+  int32_t tile_split;
 } mrdft_exec_opts;
 
 /*

@@ -33,10 +33,13 @@ OBJECTIVES = ("both", "forward", "adjoint")
 
 # kernel variants searched after the shape, per objective: (option, values);
 # the first value of each is the library default
-FWD_KNOBS = (("fwd_cb", (9, 10, 11)), ("fwd_rows_prefetch", (False, True)), ("dual_cols", (True, False)),
-             ("fwd_tree", (False, True)), ("tile_first", (True, False)))
-ADJ_KNOBS = (("adj_cb", (10, 9)), ("adj_rows13", (True, False)), ("dual_cols", (True, False)),
-             ("tile_first", (True, False)))
+FWD_KNOBS = (("fwd_cb", (9, 10, 11)), ("fwd_rows_prefetch", (False, True)), ("fwd_rows12", (False, True)),
+             ("dual_cols", (True, False)), ("fwd_tree", (False, True)))
+ADJ_KNOBS = (("adj_cb", (10, 9)), ("adj_rows13", (True, False)), ("dual_cols", (True, False)))
+# searched together with the shape (they change how the segments overlap):
+# whether the in-tile levels run as one launch, and then into how many groups
+SHAPE_SWITCHES = ("tile_first", (True, False))
+TILE_SPLITS = (1,)  # more groups measured slower: a tile launch beside the segment chains evicts their L2 data
 KEEP_MARGIN = 0.99  # a variant replaces the current choice only when at least 1% faster
 
 
@@ -171,11 +174,22 @@ def tune_plan(lengths: Sequence[int], batch: Optional[int] = None, real_input: b
             log[k] = float(timer(dict(o)))
         return log[k]
 
-    shape = tune(lengths, batch, real_input, candidates=candidates, use_cache=False, objective=objective,
-                 timer=lambda s_, k_: t({"seg_log": s_, "streams": k_}))
-    best = {"seg_log": shape[0], "streams": shape[1]}
-    best_ms = t(best)
-    for name, values in knobs_for(objective, full, shape[0]):
+    best, best_ms = None, float("inf")
+    name0, values0 = SHAPE_SWITCHES
+    for v0 in values0:
+        shape = tune(lengths, batch, real_input, candidates=candidates, use_cache=False, objective=objective,
+                     timer=lambda s_, k_: t({"seg_log": s_, "streams": k_, name0: v0}))
+        trial = {"seg_log": shape[0], "streams": shape[1], name0: v0}
+        ms = t(trial)
+        if best is None or ms < KEEP_MARGIN * best_ms:
+            best, best_ms = trial, ms
+    if best.get("tile_first") and sum(full) > (1 << best["seg_log"]):  # several segments: split the tiles
+        for k in TILE_SPLITS[1:]:
+            trial = dict(best, tile_split=k)
+            ms = t(trial)
+            if ms < KEEP_MARGIN * best_ms:
+                best, best_ms = trial, ms
+    for name, values in knobs_for(objective, full, best["seg_log"]):
         for v in values[1:]:
             trial = dict(best, **{name: v})
             ms = t(trial)

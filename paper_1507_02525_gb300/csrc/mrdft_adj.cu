@@ -433,17 +433,18 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
   }
   const int64_t w = it.window;
   const int k0 = blk << KCB;
-  // gradient pairs (2k, 2k+1): a batch of loads is issued before any store
+  // gradient pairs (2k, 2k+1): a batch of loads is issued before any store;
+  // the twiddle tables are built while the first batch is in flight
   float lsum = 0.f;  // fused loss: this thread's share
-#pragma unroll 1
-  for (int t0 = 0; t0 < PTS; t0 += 8) {
-    float4 g[8];
+  auto load_batch = [&](int t0, float4 (&g)[8]) MRDFT_INL {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int e = threadIdx.x + (t0 + t) * NT;
       const int64_t k = ((int64_t)(e >> KCB) << QB) + k0 + (e & (KC - 1));
       g[t] = adj_G<FUSED>(a, sd, i, w, 2 * k, lsum);
     }
+  };
+  auto store_batch = [&](int t0, const float4 (&g)[8]) MRDFT_INL {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int e = threadIdx.x + (t0 + t) * NT;
@@ -452,15 +453,25 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
       __stcg(a.e_out + sd.aux_off + (w << HB) + k, make_float2(g[t].x, g[t].y));
       S[stg<SA, SB>((j << CB) + k1)] = make_float2(g[t].z, -g[t].w);
     }
-  }
-  load_twq<NT>(TQ, CB, a.tw);
-  for (int t = threadIdx.x; t < KC * (64 + HU); t += NT) {
-    if (t < KC * 64) {
-      const int j = t >> 6, u = t & 63;
-      TWL[j * 65 + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * u);
-    } else {
-      const int t2 = t - KC * 64, j = t2 / HU, u = t2 % HU;
-      TWH[j * (HU + 16 / KC) + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * 64 * u);
+  };
+  {
+    float4 g[8];
+    load_batch(0, g);
+    load_twq<NT>(TQ, CB, a.tw);
+    for (int t = threadIdx.x; t < KC * (64 + HU); t += NT) {
+      if (t < KC * 64) {
+        const int j = t >> 6, u = t & 63;
+        TWL[j * 65 + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * u);
+      } else {
+        const int t2 = t - KC * 64, j = t2 / HU, u = t2 % HU;
+        TWH[j * (HU + 16 / KC) + u] = tw_any(a.tw, HB, (int64_t)(k0 + j) * 64 * u);
+      }
+    }
+    store_batch(0, g);
+#pragma unroll 1
+    for (int t0 = 8; t0 < PTS; t0 += 8) {
+      load_batch(t0, g);
+      store_batch(t0, g);
     }
   }
   __syncthreads();
@@ -505,19 +516,31 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_adj_cols(cons
   const float2* U = a.scratch + sd.aux_off + (w << HB);
   float2* acc = a.acc + 2 * sd.aux_off + (w << i);
   const bool add = sd.m > i;
-#pragma unroll 1
-  for (int t0 = 0; t0 < PTS; t0 += 8) {
-    float2 u[8];
+  // the intermediate in batches of 8 loads; the twiddle tables are built
+  // while the first batch is in flight
+  auto load_u = [&](int t0, float2 (&u)[8]) MRDFT_INL {
 #pragma unroll
     for (int t = 0; t < 8; ++t) {
       const int e = threadIdx.x + (t0 + t) * NT;
       u[t] = __ldcg(U + ((int64_t)(e >> RCB) << CB) + r0 + (e & (RC - 1)));
     }
+  };
+  auto stage_u = [&](int t0, const float2 (&u)[8]) MRDFT_INL {
 #pragma unroll
     for (int t = 0; t < 8; ++t) S[stg<6, 0>(threadIdx.x + (t0 + t) * NT)] = conjf2(u[t]);  // e = k2 RC + r
+  };
+  {
+    float2 u[8];
+    load_u(0, u);
+    load_twq<NT>(TQ, 12, a.tw);
+    for (int r = threadIdx.x; r < RC; r += NT) ZC[r] = tw_any(a.tw, i, r0 + r);
+    stage_u(0, u);
+#pragma unroll 1
+    for (int t0 = 8; t0 < PTS; t0 += 8) {
+      load_u(t0, u);
+      stage_u(t0, u);
+    }
   }
-  load_twq<NT>(TQ, 12, a.tw);
-  for (int r = threadIdx.x; r < RC; r += NT) ZC[r] = tw_any(a.tw, i, r0 + r);
   __syncthreads();
   // this block's columns of the intermediate are dead: drop them from L2
   if constexpr (RC >= 16)

@@ -684,6 +684,12 @@ void rows_launch(const FwdArgs& a, int grid, cudaStream_t s) {
       return;
     }
   }
+  if constexpr (CB == 9) {
+    if (a.rows12) {  // 2^12-point CTAs of 256 threads: twice as many, up to 4 per SM
+      rows_launch_e<CB, 12>(a, grid, s);
+      return;
+    }
+  }
   if constexpr (CB == 12) {
     if (a.rows14) {
       rows_launch_e<CB, 14>(a, grid, s);
@@ -726,6 +732,7 @@ cudaError_t set_fwd_attributes() {
     if (e == cudaSuccess) e = rows_attr<decltype(C)::value>();
   });
   if (e == cudaSuccess) e = rows_attr<12, 14>();
+  if (e == cudaSuccess) e = rows_attr<9, 12>();
   static_for_host<9, 13>([&](auto C) {
     constexpr int c = decltype(C)::value;
     if (e == cudaSuccess) e = rows_attr<c, rows_pf_e<c>(), true>();

@@ -78,6 +78,7 @@ struct FwdArgs {
   int cb_min;         // two-pass levels: C = 2^max(i - 12, cb_min), cb_min 9..11 (0 means 10)
   int rows14;         // C = 2^12 rows CTAs of 2^14 points (4 residues, 1 per SM) instead of 2^13
   int rows_pf;        // rows CTAs that copy the children into shared memory when they start
+  int rows12;         // C = 2^9 rows CTAs of 2^12 points (256 threads) instead of 2^13
   int tile_lean;      // tile CTAs in the 3-per-SM shape (work area aliasing the level buffer)
   Twiddles tw;
   int* status;

@@ -137,7 +137,12 @@ struct mrdft_plan_s {
   bool fwd_tree = false;            // off: the forward runs `top` after every segment instead
   bool tile_first = true;           // one tile launch over every segment (before them forward, after them adjoint)
   bool tile_lean = true;            // forward tile CTAs in the 3-per-SM shape
-  Launch tile_all{};                // that launch (tile_first)
+  bool fwd_rows12 = false;          // forward C = 2^9 rows CTAs of 2^12 points
+  Launch tile_all{};                // that launch (tile_first), or with tile_split > 1 ...
+  int tile_split = 1;               // ... that many launches over consecutive groups of segments
+  std::vector<Launch> tile_parts;   // the group launches (tile_first), in segment order
+  std::vector<int> seg_part;        // group of each segment
+  std::vector<cudaEvent_t> ev_tile, ev_segdone;
   std::vector<cudaEvent_t> ev_seg, ev_node;
   int seg_log = 23;
   int nstreams = 4;
@@ -278,6 +283,12 @@ void release(mrdft_plan_s* p) {
   p->ev_join.clear();
   for (cudaEvent_t e : p->ev_seg)
     if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_tile)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_segdone)
+    if (e) cudaEventDestroy(e);
+  p->ev_tile.clear();
+  p->ev_segdone.clear();
   for (cudaEvent_t e : p->ev_node)
     if (e) cudaEventDestroy(e);
   p->ev_seg.clear();
@@ -384,6 +395,7 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
   }
   std::vector<int32_t> tile_ids;
   std::vector<TileItem> tiles;
+  std::vector<Launch> seg_tiles;  // tile_first: each segment's tile items
   std::vector<LevelItem> litems;
   auto pass_blocks = [](int i) { return pass_items(i); };
   // consecutive two-pass levels (i, i + 1) of a chain, lowest first: the
@@ -443,9 +455,10 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
       T.bytes += ((int64_t)n << m) * (in_b + 8 * m);
     }
     T.count = (int)((int64_t)tiles.size() - T.off);
+    if (p->tile_first) seg_tiles.push_back(T);
     if (T.count) {
       // segments append their tile items one after another: with tile_first
-      // the union [0, tiles) is one launch
+      // the union [0, tiles) is one launch (or one per group of segments)
       if (p->tile_first) p->tile_all.bytes += T.bytes;
       else seg.chain.push_back(T);
     }
@@ -493,6 +506,22 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     p->tile_all.kind = LK_TILE;
     p->tile_all.off = 0;
     p->tile_all.count = (int)tiles.size();
+    // groups of consecutive segments, one tile launch each
+    const int ns = (int)p->segments.size();
+    const int parts = std::max(1, std::min(p->tile_split, ns));
+    p->seg_part.assign(ns, 0);
+    for (int g = 0; g < parts; ++g) {
+      const int j0 = (int)((int64_t)ns * g / parts), j1 = (int)((int64_t)ns * (g + 1) / parts);
+      Launch P{};
+      P.kind = LK_TILE;
+      P.off = j0 < ns ? seg_tiles[j0].off : (int64_t)tiles.size();
+      for (int j = j0; j < j1; ++j) {
+        P.count += seg_tiles[j].count;
+        P.bytes += seg_tiles[j].bytes;
+        p->seg_part[j] = g;
+      }
+      p->tile_parts.push_back(P);
+    }
   }
   if (p->fwd_tree && !p->top.empty()) {
     // segment of each (signal, level-S window) of the signals longer than a segment
@@ -560,6 +589,12 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     p->ev_join.push_back(e);
   }
   MRDFT_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+  if (p->tile_parts.size() > 1) {
+    p->ev_tile.assign(p->tile_parts.size(), nullptr);
+    p->ev_segdone.assign(p->segments.size(), nullptr);
+    for (auto& e : p->ev_tile) MRDFT_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (auto& e : p->ev_segdone) MRDFT_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
   if (!p->top_nodes.empty()) {
     p->ev_seg.assign(p->segments.size(), nullptr);
     p->ev_node.assign(p->top_nodes.size(), nullptr);
@@ -645,12 +680,22 @@ mrdft_status launch_fwd(mrdft_plan_s* p, FwdArgs a, const Launch& L, cudaStream_
 struct NoAfter {
   mrdft_status operator()(size_t, cudaStream_t) const { return MRDFT_OK; }
 };
-template <class F, class A = NoAfter>
-mrdft_status run_segments(mrdft_plan_s* p, cudaStream_t st, F&& chain, A&& after = NoAfter{}) {
+struct NoFork {
+  mrdft_status operator()(bool) const { return MRDFT_OK; }
+};
+// before(j, s) runs before segment j's chain is enqueued on s, after(j, s)
+// after it; forked(parallel) runs once the worker streams have forked from
+// the caller's stream (parallel) or, without workers, before the first segment
+template <class F, class A = NoAfter, class B = NoAfter, class K = NoFork>
+mrdft_status run_segments(mrdft_plan_s* p, cudaStream_t st, F&& chain, A&& after = NoAfter{}, B&& before = NoAfter{},
+                          K&& forked = NoFork{}) {
   const int nw = p->timing_serial ? 0 : (int)p->workers.size();
   if (nw <= 1) {
+    mrdft_status r0 = forked(false);
+    if (r0 != MRDFT_OK) return r0;
     for (size_t j = 0; j < p->segments.size(); ++j) {
-      mrdft_status r = chain(p->segments[j], st);
+      mrdft_status r = before(j, st);
+      if (r == MRDFT_OK) r = chain(p->segments[j], st);
       if (r == MRDFT_OK) r = after(j, st);
       if (r != MRDFT_OK) return r;
     }
@@ -658,9 +703,10 @@ mrdft_status run_segments(mrdft_plan_s* p, cudaStream_t st, F&& chain, A&& after
   }
   MRDFT_CUDA(p, cudaEventRecord(p->ev_fork, st));
   for (int k = 0; k < nw; ++k) MRDFT_CUDA(p, cudaStreamWaitEvent(p->workers[k], p->ev_fork, 0));
-  mrdft_status r = MRDFT_OK;
+  mrdft_status r = forked(true);
   for (size_t j = 0; j < p->segments.size() && r == MRDFT_OK; ++j) {
-    r = chain(p->segments[j], p->workers[j % nw]);
+    r = before(j, p->workers[j % nw]);
+    if (r == MRDFT_OK) r = chain(p->segments[j], p->workers[j % nw]);
     if (r == MRDFT_OK) r = after(j, p->workers[j % nw]);
   }
   // join every worker back even after a failed launch, so that the caller's
@@ -685,6 +731,7 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
   a.rows14 = p->fwd_rows14;
   a.rows_pf = p->fwd_rows_pf;
   a.tile_lean = p->tile_lean;
+  a.rows12 = p->fwd_rows12;
   a.tw = twiddles(p);
   a.status = p->d_status;
   if (p->n_tiny) {
@@ -694,10 +741,40 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
     t.nitems = p->n_tiny;
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_TINY, 0, st, [&] { return launch_fwd_tiny(t, p->n_tiny, st); }));
   }
-  if (p->tile_first && p->tile_all.count) {
+  // tile_first: the first group's tile launch before the fork, the others on
+  // the caller's stream after it, each segment waiting for its group's launch
+  const bool parts = p->tile_first && p->tile_parts.size() > 1;
+  if (p->tile_first && !parts && p->tile_all.count) {
     mrdft_status q = launch_fwd(p, a, p->tile_all, st);
     if (q != MRDFT_OK) return q;
   }
+  if (parts && p->tile_parts[0].count) {
+    mrdft_status q = launch_fwd(p, a, p->tile_parts[0], st);
+    if (q != MRDFT_OK) return q;
+  }
+  bool parallel = false;
+  auto forked = [&](bool par) -> mrdft_status {
+    parallel = par;
+    if (!parts || !par) return MRDFT_OK;
+    for (size_t g = 1; g < p->tile_parts.size(); ++g) {
+      if (p->tile_parts[g].count) {
+        mrdft_status q = launch_fwd(p, a, p->tile_parts[g], st);
+        if (q != MRDFT_OK) return q;
+      }
+      MRDFT_CUDA(p, cudaEventRecord(p->ev_tile[g], st));
+    }
+    return MRDFT_OK;
+  };
+  auto before = [&](size_t j, cudaStream_t s) -> mrdft_status {
+    if (!parts) return MRDFT_OK;
+    const int g = p->seg_part[j];
+    if (!parallel) {  // serial: the group's tiles right before its first segment
+      if (g > 0 && p->seg_part[j - 1] != g && p->tile_parts[g].count) return launch_fwd(p, a, p->tile_parts[g], s);
+      return MRDFT_OK;
+    }
+    if (g > 0) MRDFT_CUDA(p, cudaStreamWaitEvent(s, p->ev_tile[g], 0));
+    return MRDFT_OK;
+  };
   const bool tree = !p->top_nodes.empty();
   // forward tree: a node is enqueued right after the later of its two
   // children, on that child's stream, after an event of the other child
@@ -735,7 +812,8 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
         seg_on[j] = s;
         MRDFT_CUDA(p, cudaEventRecord(p->ev_seg[j], s));
         return child_done(p->segments[j].parent, s);
-      });
+      },
+      before, forked);
   if (r != MRDFT_OK) return r;
   if (!tree) {
     for (const Launch& L : p->top) {
@@ -825,15 +903,37 @@ mrdft_status enqueue_adjoint(mrdft_plan_s* p, const void* gy, void* gx, cudaStre
     mrdft_status r = launch_adj(p, a, *it, st, true);
     if (r != MRDFT_OK) return r;
   }
-  mrdft_status r = run_segments(p, st, [&](const Segment& seg, cudaStream_t s) {
-    for (auto it = seg.chain.rbegin(); it != seg.chain.rend(); ++it) {
-      mrdft_status q = launch_adj(p, a, *it, s, false);
-      if (q != MRDFT_OK) return q;
-    }
-    return MRDFT_OK;
-  });
+  // tile_first: the tile launch after every segment, or with tile_split > 1
+  // one launch per group of segments on the caller's stream, right after the
+  // group's last segment is enqueued, waiting for each segment of the group
+  const bool parts = p->tile_first && p->tile_parts.size() > 1;
+  bool parallel = false;
+  mrdft_status r = run_segments(
+      p, st,
+      [&](const Segment& seg, cudaStream_t s) {
+        for (auto it = seg.chain.rbegin(); it != seg.chain.rend(); ++it) {
+          mrdft_status q = launch_adj(p, a, *it, s, false);
+          if (q != MRDFT_OK) return q;
+        }
+        return MRDFT_OK;
+      },
+      [&](size_t j, cudaStream_t s) -> mrdft_status {
+        if (!parts) return MRDFT_OK;
+        const int g = p->seg_part[j];
+        const bool last = j + 1 == p->segments.size() || p->seg_part[j + 1] != g;
+        if (!parallel) return last && p->tile_parts[g].count ? launch_adj(p, a, p->tile_parts[g], s, false) : MRDFT_OK;
+        MRDFT_CUDA(p, cudaEventRecord(p->ev_segdone[j], s));
+        if (!last) return MRDFT_OK;
+        for (size_t k = 0; k <= j; ++k)
+          if (p->seg_part[k] == g) MRDFT_CUDA(p, cudaStreamWaitEvent(st, p->ev_segdone[k], 0));
+        return p->tile_parts[g].count ? launch_adj(p, a, p->tile_parts[g], st, false) : MRDFT_OK;
+      },
+      NoAfter{}, [&](bool par) -> mrdft_status {
+        parallel = par;
+        return MRDFT_OK;
+      });
   if (r != MRDFT_OK) return r;
-  if (p->tile_first && p->tile_all.count) {
+  if (p->tile_first && !parts && p->tile_all.count) {
     r = launch_adj(p, a, p->tile_all, st, false);
     if (r != MRDFT_OK) return r;
   }
@@ -942,10 +1042,12 @@ mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_
   if (o.streams < 0 || o.streams > 16) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: streams must be in [0, 16]");
   if (o.fwd_cb != 0 && (o.fwd_cb < 9 || o.fwd_cb > 11))
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: fwd_cb must be 0 or in [9, 11]");
+  if (o.tile_split < 0 || o.tile_split > 64)
+    return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: tile_split must be in [0, 64]");
   if (o.adj_cb != 0 && (o.adj_cb < 9 || o.adj_cb > 10))
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: adj_cb must be 0 or in [9, 10]");
   if (!sw(o.fwd_rows_prefetch) || !sw(o.fwd_rows14) || !sw(o.adj_rows13) || !sw(o.dual_cols) || !sw(o.fwd_tree) ||
-      !sw(o.tile_first) || !sw(o.tile_lean))
+      !sw(o.tile_first) || !sw(o.tile_lean) || !sw(o.fwd_rows12))
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: switches must be MRDFT_OPT_DEFAULT, _OFF or _ON");
   if (!lengths) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: lengths is NULL");
   if (batch < 1 || batch > (int64_t(1) << 30))
@@ -978,6 +1080,7 @@ mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_
   auto on = [](int32_t v, bool dflt) { return v == MRDFT_OPT_DEFAULT ? dflt : v == MRDFT_OPT_ON; };
   if (o.fwd_cb) p->fwd_cb_min = o.fwd_cb;
   if (o.adj_cb) p->adj_cb_min = o.adj_cb;
+  if (o.tile_split) p->tile_split = o.tile_split;
   p->fwd_rows_pf = on(o.fwd_rows_prefetch, p->fwd_rows_pf != 0);
   p->fwd_rows14 = on(o.fwd_rows14, p->fwd_rows14 != 0);
   p->adj_rows13 = on(o.adj_rows13, p->adj_rows13 != 0);
@@ -985,6 +1088,7 @@ mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_
   p->fwd_tree = on(o.fwd_tree, p->fwd_tree);
   p->tile_first = on(o.tile_first, p->tile_first);
   p->tile_lean = on(o.tile_lean, p->tile_lean);
+  p->fwd_rows12 = on(o.fwd_rows12, p->fwd_rows12);
   mrdft_status st = build_plan(p, lengths, n_lengths, batch);
   if (st != MRDFT_OK) {
     fail(nullptr, st, p->err);
@@ -1010,6 +1114,8 @@ mrdft_status mrdft_plan_get_opts(mrdft_plan_t p, mrdft_exec_opts* opts) {
   opts->fwd_tree = sw(p->fwd_tree);
   opts->tile_first = sw(p->tile_first);
   opts->tile_lean = sw(p->tile_lean);
+  opts->fwd_rows12 = sw(p->fwd_rows12);
+  opts->tile_split = p->tile_split;
   return MRDFT_OK;
 }
 
@@ -1115,7 +1221,14 @@ mrdft_status mrdft_plan_info(mrdft_plan_t p, int32_t* tile_log, int32_t* fwd_lau
   };
   for (const Segment& g : p->segments)
     for (const Launch& L : g.chain) count(L);
-  if (p->tile_first && p->tile_all.count) count(p->tile_all);
+  if (p->tile_first) {
+    if (p->tile_parts.size() > 1) {
+      for (const Launch& L : p->tile_parts)
+        if (L.count) count(L);
+    } else if (p->tile_all.count) {
+      count(p->tile_all);
+    }
+  }
   if (p->top_nodes.empty()) {
     for (const Launch& L : p->top) count(L);
   } else {

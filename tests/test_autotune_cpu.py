@@ -101,16 +101,19 @@ def test_tune_plan_searches_kernel_variants(tmp_path, monkeypatch):
 
     best = autotune.tune_plan([1 << 24], 1, objective="forward", timer=timer,
                               candidates=[(20, 4), (21, 2), (22, 4)])
-    assert best == {"seg_log": 21, "streams": 2, "fwd_cb": 10, "fwd_tree": True}
+    assert best == {"seg_log": 21, "streams": 2, "tile_first": True, "fwd_cb": 10, "fwd_tree": True}
     names = {k for o in seen for k in o}
     assert {"fwd_cb", "fwd_rows_prefetch", "dual_cols", "fwd_tree", "tile_first"} <= names
+    # the shape is searched with the in-tile levels both as one launch and per segment
+    assert {(o["seg_log"], o.get("tile_first")) for o in seen} >= {(20, True), (20, False), (22, False)}
     assert not any("adj_cb" in o for o in seen)
     n = len(seen)
     assert autotune.tune_plan([1 << 24], 1, objective="forward", timer=lambda o: 1 / 0) == best
     assert len(seen) == n  # cached
-    adj = autotune.tune_plan([1 << 24], 1, objective="adjoint", timer=lambda o: float(o.get("adj_cb", 10)),
+    adj = autotune.tune_plan([1 << 24], 1, objective="adjoint",
+                             timer=lambda o: float(o.get("adj_cb", 10)) - (0.5 if o.get("tile_first") is False else 0),
                              candidates=[(21, 2)])
-    assert adj == {"seg_log": 21, "streams": 2, "adj_cb": 9}
+    assert adj == {"seg_log": 21, "streams": 2, "tile_first": False, "adj_cb": 9}
     data = json.loads((tmp_path / "tune.json").read_text())
     assert sum(1 for k in data if k.endswith("|forward|opts")) == 1
     assert sum(1 for k in data if k.endswith("|adjoint|opts")) == 1

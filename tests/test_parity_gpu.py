@@ -839,3 +839,45 @@ def test_tile_lean_forward(oracle, real):
     ys = split_out(run_forward(plan, x), lengths)
     for s, xs in enumerate(split_in(x, lengths)):
         check_forward_levels(ys[s], oracle.forward(xs.astype(np.complex128)), xs, f"lean s={s} N={len(xs)}")
+
+
+@pytest.mark.parametrize("m", [15, 16, 19, 21])
+def test_forward_rows12(oracle, m):
+    """fwd_rows12: the C = 2^9 two-pass levels in rows CTAs of 2^12 points."""
+    N = 1 << m
+    x = inputs.complex_signals(2, N, seed=600 + m)
+    y = run_forward(_lib.Plan([N], 2, seg_log=20, opts={"fwd_rows12": True}), x.reshape(-1)).reshape(2, m, N)
+    for s in range(2):
+        check_forward_levels(y[s], oracle.forward(x[s].astype(np.complex128)), x[s], f"rows12 m={m} s={s}")
+
+
+@pytest.mark.parametrize("split,seg_log,streams", [(2, 14, 3), (3, 15, 2), (4, 16, 4), (8, 13, 1)])
+def test_tile_split_both_directions(oracle, split, seg_log, streams):
+    """tile_split: the in-tile levels as several launches over groups of
+    segments -- each forward segment waits only for its own group's tiles, each
+    adjoint tile group only for its own segments -- repeated under graph replay."""
+    lengths = [1 << 18, 1 << 12, 1 << 16, 1 << 9, 1 << 15, 1 << 13, 1 << 17]
+    x = inputs.complex_signals(1, sum(lengths), seed=707)[0]
+    gy = None
+    plan = _lib.Plan(lengths, len(lengths), graph=True, seg_log=seg_log, streams=streams,
+                     opts={"tile_first": True, "tile_split": split})
+    assert plan.opts()["tile_split"] == split
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty(plan.out_elems, dtype=torch.complex64, device="cuda")
+    gx = torch.empty(plan.in_elems, dtype=torch.complex64, device="cuda")
+    gy = inputs.complex_signals(1, plan.out_elems, seed=708)[0]
+    gyt = torch.from_numpy(gy).cuda()
+    sp = torch.cuda.current_stream().cuda_stream
+    for _ in range(3):
+        y.fill_(float("nan"))
+        gx.fill_(float("nan"))
+        plan.forward(xt.data_ptr(), y.data_ptr(), sp)
+        plan.adjoint(gyt.data_ptr(), gx.data_ptr(), sp)
+    torch.cuda.synchronize()
+    plan.status_poll()
+    ys = split_out(y.cpu().numpy(), lengths)
+    gxs = split_in(gx.cpu().numpy(), lengths)
+    gys = split_out(gy, lengths)
+    for s, xs in enumerate(split_in(x, lengths)):
+        check_forward_levels(ys[s], oracle.forward(xs.astype(np.complex128)), xs, f"split={split} s={s}")
+        check_adjoint(gxs[s], oracle.adjoint(gys[s].astype(np.complex128)), gys[s], f"split={split} s={s}")
