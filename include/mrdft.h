@@ -139,6 +139,11 @@ mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t 
  *              group's segments start (forward) as soon as its own tiles are
  *              done, while the next group's tiles run; in the adjoint a
  *              group's tiles start as soon as its segments are done
+ *   top_cols_early : the forward runs the cols passes of the levels above
+ *              the segment size on a stream of their own while the segments
+ *              run (they read only x), each into its own scratch (N/2 complex
+ *              per signal and level); their rows passes stay at the end
+ *              (default off)
  */
 #define MRDFT_OPT_DEFAULT 0
 #define MRDFT_OPT_OFF 1
@@ -157,6 +162,7 @@ typedef struct {
   int32_t tile_lean;
   int32_t fwd_rows12;
   int32_t tile_split;
+  int32_t top_cols_early;
 } mrdft_exec_opts;
 
 /*

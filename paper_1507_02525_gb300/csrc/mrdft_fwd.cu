@@ -426,11 +426,25 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_fwd_cols(cons
       xa[t] = load_x1_stream(a, xs + n);
       xb[t] = load_x1_stream(a, xs + h + n);
     }
+    if constexpr (NT >= RC) {
+      // every point of this thread has the thread's column r and q = q_tid +
+      // (t0 + t) NT / RC, so w_{2Q}^q = w_{2Q}^(q_tid) w_32^(t0 + t) (2Q RC / NT
+      // = 32): one lookup per thread, compile-time factors per point
+      static_assert((1 << (E + 1)) / NT == 32 && PTS == 16, "w_32 steps over two batches of 8");
+      const float2 w0 = cmul(ZC[threadIdx.x & (RC - 1)], twq_l(tw, QB + 1, threadIdx.x >> RCB));
+      const float2 wb = t0 ? cmul_mj(w0) : w0;  // w_32^8 = -j
+      static_for<0, 8>([&](auto TT) MRDFT_INL {
+        constexpr int t = decltype(TT)::value;
+        const int e = threadIdx.x + (t0 + t) * NT;
+        S[stg<6, 0>(e)] = cmul(csub(xa[t], xb[t]), cmul_ct<32, t>(wb));  // e = q RC + r
+      });
+    } else {
 #pragma unroll
-    for (int t = 0; t < 8; ++t) {
-      const int e = threadIdx.x + (t0 + t) * NT;
-      const float2 w = cmul(ZC[e & (RC - 1)], twq_l(tw, QB + 1, e >> RCB));
-      S[stg<6, 0>(e)] = cmul(csub(xa[t], xb[t]), w);  // e = q RC + r
+      for (int t = 0; t < 8; ++t) {
+        const int e = threadIdx.x + (t0 + t) * NT;
+        const float2 w = cmul(ZC[e & (RC - 1)], twq_l(tw, QB + 1, e >> RCB));
+        S[stg<6, 0>(e)] = cmul(csub(xa[t], xb[t]), w);  // e = q RC + r
+      }
     }
   }
   __syncthreads();

@@ -138,6 +138,14 @@ struct mrdft_plan_s {
   bool tile_first = true;           // one tile launch over every segment (before them forward, after them adjoint)
   bool tile_lean = true;            // forward tile CTAs in the 3-per-SM shape
   bool fwd_rows12 = false;          // forward C = 2^9 rows CTAs of 2^12 points
+  // top_cols_early: the cols passes of the unpaired levels above the segment
+  // size run on their own stream during the segment chains (they read only
+  // x), each into its own scratch; their rows passes stay at the end
+  bool top_cols_early = false;
+  float2* d_scratch_top = nullptr;  // half_elems per early level
+  std::vector<int> top_early;       // index into `top` of each early level (its scratch slot follows)
+  cudaStream_t early = nullptr;
+  cudaEvent_t ev_early_go = nullptr, ev_early_done = nullptr;
   Launch tile_all{};                // that launch (tile_first), or with tile_split > 1 ...
   int tile_split = 1;               // ... that many launches over consecutive groups of segments
   std::vector<Launch> tile_parts;   // the group launches (tile_first), in segment order
@@ -295,6 +303,11 @@ void release(mrdft_plan_s* p) {
   p->ev_node.clear();
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   p->ev_fork = nullptr;
+  if (p->early) cudaStreamDestroy(p->early);
+  if (p->ev_early_go) cudaEventDestroy(p->ev_early_go);
+  if (p->ev_early_done) cudaEventDestroy(p->ev_early_done);
+  p->early = nullptr;
+  p->ev_early_go = p->ev_early_done = nullptr;
   for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
   p->event_pool.clear();
   for (auto& g : p->fwd_graphs) cudaGraphExecDestroy(g.exec);
@@ -303,7 +316,7 @@ void release(mrdft_plan_s* p) {
   p->adj_graphs.clear();
   void* ptrs[] = {p->d_sigs, p->d_tile_ids, p->d_tiles, p->d_tiny_ids, p->d_levels, p->d_br,
                   p->d_tw13, p->d_twlo, p->d_twhi, p->d_scratch, p->d_e0,
-                  p->d_e1, p->d_etop, p->d_acc, p->d_status, p->d_stage_x, p->d_stage_y};
+                  p->d_e1, p->d_etop, p->d_acc, p->d_status, p->d_stage_x, p->d_stage_y, p->d_scratch_top};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -502,6 +515,9 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     if (L.count) p->top.push_back(L);
   }
   pair_levels(p->top);
+  if (p->top_cols_early && !p->fwd_tree)
+    for (size_t k = 0; k < p->top.size(); ++k)
+      if (p->top[k].kind == LK_PASS && p->top[k].dual == 0) p->top_early.push_back((int)k);
   if (p->tile_first) {
     p->tile_all.kind = LK_TILE;
     p->tile_all.off = 0;
@@ -589,6 +605,11 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     p->ev_join.push_back(e);
   }
   MRDFT_CUDA(p, cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+  if (!p->top_early.empty()) {
+    MRDFT_CUDA(p, cudaStreamCreateWithFlags(&p->early, cudaStreamNonBlocking));
+    MRDFT_CUDA(p, cudaEventCreateWithFlags(&p->ev_early_go, cudaEventDisableTiming));
+    MRDFT_CUDA(p, cudaEventCreateWithFlags(&p->ev_early_done, cudaEventDisableTiming));
+  }
   if (p->tile_parts.size() > 1) {
     p->ev_tile.assign(p->tile_parts.size(), nullptr);
     p->ev_segdone.assign(p->segments.size(), nullptr);
@@ -628,6 +649,7 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     if (e == cudaSuccess) e = cudaMalloc(&p->d_e1, half);
     if (e == cudaSuccess && !p->top.empty()) e = cudaMalloc(&p->d_etop, half);
     if (e == cudaSuccess) e = cudaMalloc(&p->d_acc, 2 * half);
+    if (e == cudaSuccess && !p->top_early.empty()) e = cudaMalloc(&p->d_scratch_top, p->top_early.size() * half);
     if (e != cudaSuccess) return fail(p, MRDFT_ENOMEM, std::string("scratch allocation: ") + cudaGetErrorString(e));
   }
   MRDFT_CUDA(p, cudaMalloc(&p->d_status, sizeof(int)));
@@ -638,7 +660,10 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
 
 Twiddles twiddles(const mrdft_plan_s* p) { return Twiddles{p->d_tw13, p->d_twlo, p->d_twhi}; }
 
-mrdft_status launch_fwd(mrdft_plan_s* p, FwdArgs a, const Launch& L, cudaStream_t st) {
+// passes: 1 the cols pass only, 2 the rows pass only, 3 both (two-pass
+// levels); scr: the intermediate (nullptr: half (level & 1) of the scratch)
+mrdft_status launch_fwd(mrdft_plan_s* p, FwdArgs a, const Launch& L, cudaStream_t st, int passes = 3,
+                        float2* scr = nullptr) {
   a.level = L.level;
   a.nitems = L.count;
   if (L.kind == LK_TILE) {
@@ -651,8 +676,10 @@ mrdft_status launch_fwd(mrdft_plan_s* p, FwdArgs a, const Launch& L, cudaStream_
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_WINDOW, L.bytes, st, [&] { return launch_fwd_window(a, L.count, st); }));
   } else {
     // the two-pass intermediate of level i lives in half (i & 1) of the scratch
-    a.scratch = p->d_scratch + (L.level & 1) * p->half_elems;
-    if (L.dual == 1) {
+    a.scratch = scr ? scr : p->d_scratch + (L.level & 1) * p->half_elems;
+    if (!(passes & 1)) {
+      // cols pass already run
+    } else if (L.dual == 1) {
       FwdArgs d = a;
       d.level = L.level + 1;
       d.nitems = L.c2_count;
@@ -670,7 +697,8 @@ mrdft_status launch_fwd(mrdft_plan_s* p, FwdArgs a, const Launch& L, cudaStream_
       MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_COLS, 0, st, [&] { return launch_fwd_cols(a, L.count, st); }));
     }
     a.items = p->d_levels + L.off;
-    MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_ROWS, L.bytes, st, [&] { return launch_fwd_rows(a, L.count, st); }));
+    if (passes & 2)
+      MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_ROWS, L.bytes, st, [&] { return launch_fwd_rows(a, L.count, st); }));
   }
   return MRDFT_OK;
 }
@@ -775,6 +803,24 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
     if (g > 0) MRDFT_CUDA(p, cudaStreamWaitEvent(s, p->ev_tile[g], 0));
     return MRDFT_OK;
   };
+  // top_cols_early: the top levels' cols passes on their own stream, from here on
+  const bool early = !p->top_early.empty();
+  auto early_scr = [&](size_t j) { return p->d_scratch_top + (int64_t)j * p->half_elems; };
+  if (early) {
+    const bool par = !p->timing_serial;
+    cudaStream_t es = par ? p->early : st;
+    if (par) {
+      MRDFT_CUDA(p, cudaEventRecord(p->ev_early_go, st));
+      MRDFT_CUDA(p, cudaStreamWaitEvent(es, p->ev_early_go, 0));
+    }
+    for (size_t j = 0; j < p->top_early.size(); ++j) {
+      mrdft_status q = launch_fwd(p, a, p->top[p->top_early[j]], es, 1, early_scr(j));
+      if (q != MRDFT_OK) return q;
+    }
+    if (par) {
+      MRDFT_CUDA(p, cudaEventRecord(p->ev_early_done, es));
+    }
+  }
   const bool tree = !p->top_nodes.empty();
   // forward tree: a node is enqueued right after the later of its two
   // children, on that child's stream, after an event of the other child
@@ -815,9 +861,12 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
       },
       before, forked);
   if (r != MRDFT_OK) return r;
+  if (early && !p->timing_serial) MRDFT_CUDA(p, cudaStreamWaitEvent(st, p->ev_early_done, 0));
   if (!tree) {
-    for (const Launch& L : p->top) {
-      r = launch_fwd(p, a, L, st);
+    for (size_t k = 0; k < p->top.size(); ++k) {
+      size_t j = 0;
+      while (j < p->top_early.size() && p->top_early[j] != (int)k) ++j;
+      r = j < p->top_early.size() ? launch_fwd(p, a, p->top[k], st, 2, early_scr(j)) : launch_fwd(p, a, p->top[k], st);
       if (r != MRDFT_OK) return r;
     }
   }
@@ -1047,7 +1096,7 @@ mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_
   if (o.adj_cb != 0 && (o.adj_cb < 9 || o.adj_cb > 10))
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: adj_cb must be 0 or in [9, 10]");
   if (!sw(o.fwd_rows_prefetch) || !sw(o.fwd_rows14) || !sw(o.adj_rows13) || !sw(o.dual_cols) || !sw(o.fwd_tree) ||
-      !sw(o.tile_first) || !sw(o.tile_lean) || !sw(o.fwd_rows12))
+      !sw(o.tile_first) || !sw(o.tile_lean) || !sw(o.fwd_rows12) || !sw(o.top_cols_early))
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: switches must be MRDFT_OPT_DEFAULT, _OFF or _ON");
   if (!lengths) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: lengths is NULL");
   if (batch < 1 || batch > (int64_t(1) << 30))
@@ -1089,6 +1138,7 @@ mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_
   p->tile_first = on(o.tile_first, p->tile_first);
   p->tile_lean = on(o.tile_lean, p->tile_lean);
   p->fwd_rows12 = on(o.fwd_rows12, p->fwd_rows12);
+  p->top_cols_early = on(o.top_cols_early, p->top_cols_early);
   mrdft_status st = build_plan(p, lengths, n_lengths, batch);
   if (st != MRDFT_OK) {
     fail(nullptr, st, p->err);
@@ -1116,6 +1166,7 @@ mrdft_status mrdft_plan_get_opts(mrdft_plan_t p, mrdft_exec_opts* opts) {
   opts->tile_lean = sw(p->tile_lean);
   opts->fwd_rows12 = sw(p->fwd_rows12);
   opts->tile_split = p->tile_split;
+  opts->top_cols_early = sw(p->top_cols_early);
   return MRDFT_OK;
 }
 

@@ -881,3 +881,26 @@ def test_tile_split_both_directions(oracle, split, seg_log, streams):
     for s, xs in enumerate(split_in(x, lengths)):
         check_forward_levels(ys[s], oracle.forward(xs.astype(np.complex128)), xs, f"split={split} s={s}")
         check_adjoint(gxs[s], oracle.adjoint(gys[s].astype(np.complex128)), gys[s], f"split={split} s={s}")
+
+
+@pytest.mark.parametrize("seg_log,streams", [(14, 3), (16, 1), (18, 4)])
+def test_top_cols_early(oracle, seg_log, streams):
+    """top_cols_early: the cols passes of the levels above the segment size run
+    on their own stream during the segments, each into its own scratch, and
+    their rows passes at the end -- under graph replay, repeated."""
+    lengths = [1 << 20, 1 << 17, 1 << 19, 1 << 13]
+    x = inputs.complex_signals(1, sum(lengths), seed=808)[0]
+    plan = _lib.Plan(lengths, len(lengths), graph=True, seg_log=seg_log, streams=streams,
+                     opts={"top_cols_early": True})
+    assert plan.opts()["top_cols_early"] is True
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty(plan.out_elems, dtype=torch.complex64, device="cuda")
+    sp = torch.cuda.current_stream().cuda_stream
+    for _ in range(3):
+        y.fill_(float("nan"))
+        plan.forward(xt.data_ptr(), y.data_ptr(), sp)
+    torch.cuda.synchronize()
+    plan.status_poll()
+    ys = split_out(y.cpu().numpy(), lengths)
+    for s, xs in enumerate(split_in(x, lengths)):
+        check_forward_levels(ys[s], oracle.forward(xs.astype(np.complex128)), xs, f"early S={seg_log} s={s}")
