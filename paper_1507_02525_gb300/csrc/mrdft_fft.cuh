@@ -11,11 +11,11 @@
 //
 // Shared layout (no padding): element a of the work buffer lives at
 // zlay<ZS>(a), an XOR permutation inside every aligned block of 16 elements
-// chosen so that, for 8-byte accesses, every half-warp of a pass touches 16
-// distinct bank pairs both when it reads 8 consecutive elements per lane and
-// when it writes lane-consecutive elements; ZS = log2 of the number of
-// interleaved sequences for position-major storage (capped at 4), 0 for
-// sequence-major storage.  The first pass reads its input through src();
+// chosen so that every pass's reads (8 consecutive elements per lane) and
+// writes (lane-consecutive elements) are free of bank conflicts; ZS = log2 of
+// the number of interleaved sequences for position-major storage (capped at
+// 4), 0 for sequence-major storage (16-byte chunks permuted, read four
+// chunks at a time).  The first pass reads its input through src();
 // callers that stage the input in shared memory use an XOR layout stg<A,B>()
 // there, picked per FFT shape so that the digit-reversed read of the first
 // pass is conflict-free; the first pass then rewrites the buffer in place.
@@ -26,9 +26,17 @@
 
 namespace mrdft {
 
+// Work-buffer layouts.  Sequence-major storage (ZS = 0) permutes 16-byte
+// chunks: element a of row a >> 4 (16 elements, 128 bytes) keeps its half
+// a & 1 of chunk (a >> 1) & 7, and the chunk moves to chunk ^ (row & 7).  A
+// pass's group of 8 consecutive elements then stays in 4 whole chunks, read
+// with four 16-byte loads (every quarter-warp touches 8 distinct chunks), and
+// lane-consecutive 8-byte stores stay conflict-free.  Position-major storage
+// of 2^ZS interleaved sequences (ZS >= 1) XORs the low element bits.
 template <int ZS>
 __device__ __forceinline__ int zlay(int a) {
   if constexpr (ZS >= 4) return a;
+  else if constexpr (ZS == 0) return a ^ (((a >> 4) & 7) << 1);
   else return a ^ (((a >> (3 + ZS)) & ((1 << (4 - ZS)) - 1)) << ZS);
 }
 // staging layout: the low 4 index bits XOR bits A.. (and B.., B > 0)
@@ -178,8 +186,20 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
         }
       } else {
         const int a0 = SEQ_MINOR ? (((g << RB) << nseq_log) + b) : ((b << LB) + (g << RB));
+        if constexpr (!SEQ_MINOR && ZS == 0 && R == 8) {
+          // 8 consecutive elements = chunks c0 .. c0 + 3 of row a0 >> 4 (c0 = 0 or 4)
+          const float2* rowp = Z + ((a0 >> 4) << 4);
+          const int x = (a0 >> 4) & 7, c0 = (a0 >> 1) & 7;
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[j][r] = Z[zlay<ZS>(a0 + (SEQ_MINOR ? (r << nseq_log) : r))];
+          for (int q = 0; q < 4; ++q) {
+            const float4 t = *reinterpret_cast<const float4*>(rowp + (((c0 + q) ^ x) << 1));
+            v[j][2 * q] = make_float2(t.x, t.y);
+            v[j][2 * q + 1] = make_float2(t.z, t.w);
+          }
+        } else {
+#pragma unroll
+          for (int r = 0; r < R; ++r) v[j][r] = Z[zlay<ZS>(a0 + (SEQ_MINOR ? (r << nseq_log) : r))];
+        }
       }
       const int tg = g >> SH;
       if (tg != 0) {
