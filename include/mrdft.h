@@ -144,6 +144,12 @@ mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t 
  *              run (they read only x), each into its own scratch (N/2 complex
  *              per signal and level); their rows passes stay at the end
  *              (default off)
+ *   top_overlap : the forward runs the cols passes of the levels above the
+ *              segment size on a stream of their own (from the end of the
+ *              segments, or from the start with top_cols_early), each into
+ *              its own scratch, and each level's rows pass waits only for
+ *              its own cols pass: the cols pass of a level overlaps the rows
+ *              pass of the level below (default off)
  */
 #define MRDFT_OPT_DEFAULT 0
 #define MRDFT_OPT_OFF 1
@@ -163,6 +169,7 @@ typedef struct {
   int32_t fwd_rows12;
   int32_t tile_split;
   int32_t top_cols_early;
+  int32_t top_overlap;
 } mrdft_exec_opts;
 
 /*

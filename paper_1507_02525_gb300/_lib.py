@@ -46,9 +46,10 @@ class ExecOpts(ctypes.Structure):
     """mrdft_exec_opts (include/mrdft.h): 0 = library default; switches 1 = off, 2 = on."""
     _fields_ = [(n, ctypes.c_int32) for n in ("seg_log", "streams", "fwd_cb", "adj_cb", "fwd_rows_prefetch",
                                                "fwd_rows14", "adj_rows13", "dual_cols", "fwd_tree", "tile_first",
-                                               "tile_lean", "fwd_rows12", "tile_split", "top_cols_early")]
+                                               "tile_lean", "fwd_rows12", "tile_split", "top_cols_early",
+                                               "top_overlap")]
     SWITCHES = ("fwd_rows_prefetch", "fwd_rows14", "adj_rows13", "dual_cols", "fwd_tree", "tile_first", "tile_lean",
-                "fwd_rows12", "top_cols_early")
+                "fwd_rows12", "top_cols_early", "top_overlap")
 
     @classmethod
     def from_dict(cls, d):

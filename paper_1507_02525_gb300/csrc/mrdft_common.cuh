@@ -193,11 +193,17 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
 }
 
-// L2 policy that keeps lines resident ahead of normal and evict-first data,
-// and an 8-byte store that carries it.
+// L2 policies that keep lines resident ahead of normal and evict-first data
+// (evict_last), or let them go first (evict_first), and an 8-byte store that
+// carries one.
 __device__ __forceinline__ uint64_t l2_evict_last_policy() {
   uint64_t pol;
   asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;\n" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_evict_first_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;\n" : "=l"(pol));
   return pol;
 }
 __device__ __forceinline__ void st_l2_keep(float2* p, float2 v, uint64_t pol) {

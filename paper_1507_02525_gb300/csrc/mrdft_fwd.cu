@@ -451,7 +451,8 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_fwd_cols(cons
   float2* F = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
   auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[stg<6, 0>((n << RCB) + b)]; };
   // the intermediate is read by the rows pass right after: keep it in L2
-  const uint64_t keep = l2_evict_last_policy();
+  // (f_late: the rows pass comes much later; let it leave L2 first instead)
+  const uint64_t keep = a.f_late ? l2_evict_first_policy() : l2_evict_last_policy();
   auto sink = [&](int, int b, int k2, float2 v) MRDFT_INL { st_l2_keep(F + ((int64_t)k2 << CB) + r0 + b, v, keep); };
   cg_fft<QB, QB, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, NoPre{}, sink);
 }

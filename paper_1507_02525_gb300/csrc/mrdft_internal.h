@@ -80,6 +80,7 @@ struct FwdArgs {
   int rows_pf;        // rows CTAs that copy the children into shared memory when they start
   int rows12;         // C = 2^9 rows CTAs of 2^12 points (256 threads) instead of 2^13
   int tile_lean;      // tile CTAs in the 3-per-SM shape (work area aliasing the level buffer)
+  int f_late;         // cols: the intermediate is read long after (stored evict-first in L2, not evict-last)
   Twiddles tw;
   int* status;
 };

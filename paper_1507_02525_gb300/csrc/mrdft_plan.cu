@@ -142,10 +142,15 @@ struct mrdft_plan_s {
   // size run on their own stream during the segment chains (they read only
   // x), each into its own scratch; their rows passes stay at the end
   bool top_cols_early = false;
+  // top_overlap: those cols passes on their own stream as well (from the end
+  // of the segments unless top_cols_early), each level's rows pass waiting
+  // only for its own cols pass (one event per level)
+  bool top_overlap = false;
   float2* d_scratch_top = nullptr;  // half_elems per early level
   std::vector<int> top_early;       // index into `top` of each early level (its scratch slot follows)
   cudaStream_t early = nullptr;
   cudaEvent_t ev_early_go = nullptr, ev_early_done = nullptr;
+  std::vector<cudaEvent_t> ev_top_cols;  // top_overlap: after the cols pass of early level j
   Launch tile_all{};                // that launch (tile_first), or with tile_split > 1 ...
   int tile_split = 1;               // ... that many launches over consecutive groups of segments
   std::vector<Launch> tile_parts;   // the group launches (tile_first), in segment order
@@ -306,6 +311,9 @@ void release(mrdft_plan_s* p) {
   if (p->early) cudaStreamDestroy(p->early);
   if (p->ev_early_go) cudaEventDestroy(p->ev_early_go);
   if (p->ev_early_done) cudaEventDestroy(p->ev_early_done);
+  for (cudaEvent_t e : p->ev_top_cols)
+    if (e) cudaEventDestroy(e);
+  p->ev_top_cols.clear();
   p->early = nullptr;
   p->ev_early_go = p->ev_early_done = nullptr;
   for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
@@ -515,7 +523,7 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     if (L.count) p->top.push_back(L);
   }
   pair_levels(p->top);
-  if (p->top_cols_early && !p->fwd_tree)
+  if ((p->top_cols_early || p->top_overlap) && !p->fwd_tree)
     for (size_t k = 0; k < p->top.size(); ++k)
       if (p->top[k].kind == LK_PASS && p->top[k].dual == 0) p->top_early.push_back((int)k);
   if (p->tile_first) {
@@ -609,6 +617,10 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     MRDFT_CUDA(p, cudaStreamCreateWithFlags(&p->early, cudaStreamNonBlocking));
     MRDFT_CUDA(p, cudaEventCreateWithFlags(&p->ev_early_go, cudaEventDisableTiming));
     MRDFT_CUDA(p, cudaEventCreateWithFlags(&p->ev_early_done, cudaEventDisableTiming));
+    if (p->top_overlap) {
+      p->ev_top_cols.assign(p->top_early.size(), nullptr);
+      for (auto& e : p->ev_top_cols) MRDFT_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
   }
   if (p->tile_parts.size() > 1) {
     p->ev_tile.assign(p->tile_parts.size(), nullptr);
@@ -803,23 +815,50 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
     if (g > 0) MRDFT_CUDA(p, cudaStreamWaitEvent(s, p->ev_tile[g], 0));
     return MRDFT_OK;
   };
-  // top_cols_early: the top levels' cols passes on their own stream, from here on
+  // the top levels' cols passes on their own stream (top_cols_early: from
+  // here on; top_overlap alone: from the end of the segments)
   const bool early = !p->top_early.empty();
+  const bool early_par = early && !p->timing_serial;
+  const bool per_level = early_par && !p->ev_top_cols.empty();
   auto early_scr = [&](size_t j) { return p->d_scratch_top + (int64_t)j * p->half_elems; };
-  if (early) {
-    const bool par = !p->timing_serial;
-    cudaStream_t es = par ? p->early : st;
-    if (par) {
+  bool early_forked = false;
+  // an error after the fork still joins the early stream (stream capture
+  // must end with every forked stream joined)
+  auto join_on_error = [&](mrdft_status q) {
+    if (early_forked) {
+      cudaEventRecord(p->ev_early_done, p->early);
+      cudaStreamWaitEvent(st, p->ev_early_done, 0);
+      early_forked = false;
+    }
+    return q;
+  };
+  auto start_early = [&]() -> mrdft_status {
+    cudaStream_t es = early_par ? p->early : st;
+    if (early_par) {
       MRDFT_CUDA(p, cudaEventRecord(p->ev_early_go, st));
       MRDFT_CUDA(p, cudaStreamWaitEvent(es, p->ev_early_go, 0));
+      early_forked = true;
     }
+    // during the segments (top_cols_early) the intermediates wait for the
+    // end: stored evict-first so that they do not push the segments' data
+    // out of L2
+    FwdArgs ea = a;
+    ea.f_late = p->top_cols_early ? 1 : 0;
     for (size_t j = 0; j < p->top_early.size(); ++j) {
-      mrdft_status q = launch_fwd(p, a, p->top[p->top_early[j]], es, 1, early_scr(j));
-      if (q != MRDFT_OK) return q;
+      mrdft_status q = launch_fwd(p, ea, p->top[p->top_early[j]], es, 1, early_scr(j));
+      if (q != MRDFT_OK) return join_on_error(q);
+      if (per_level) {
+        const cudaError_t e = cudaEventRecord(p->ev_top_cols[j], es);
+        if (e != cudaSuccess) return join_on_error(cuda_fail(p, e, "cudaEventRecord(ev_top_cols)"));
+      }
     }
-    if (par) {
-      MRDFT_CUDA(p, cudaEventRecord(p->ev_early_done, es));
-    }
+    if (early_par && !per_level) MRDFT_CUDA(p, cudaEventRecord(p->ev_early_done, es));
+    return MRDFT_OK;
+  };
+  const bool early_at_start = early && p->top_cols_early;
+  if (early_at_start) {
+    mrdft_status q = start_early();
+    if (q != MRDFT_OK) return q;
   }
   const bool tree = !p->top_nodes.empty();
   // forward tree: a node is enqueued right after the later of its two
@@ -860,14 +899,28 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
         return child_done(p->segments[j].parent, s);
       },
       before, forked);
-  if (r != MRDFT_OK) return r;
-  if (early && !p->timing_serial) MRDFT_CUDA(p, cudaStreamWaitEvent(st, p->ev_early_done, 0));
+  if (r != MRDFT_OK) return join_on_error(r);
+  if (early && !early_at_start) {
+    r = start_early();
+    if (r != MRDFT_OK) return r;
+  }
+  if (early_par && !per_level) MRDFT_CUDA(p, cudaStreamWaitEvent(st, p->ev_early_done, 0));
   if (!tree) {
+    // with per-level events the caller's stream joins the early stream at
+    // the wait for its last cols pass (nothing is enqueued there after it)
     for (size_t k = 0; k < p->top.size(); ++k) {
       size_t j = 0;
       while (j < p->top_early.size() && p->top_early[j] != (int)k) ++j;
-      r = j < p->top_early.size() ? launch_fwd(p, a, p->top[k], st, 2, early_scr(j)) : launch_fwd(p, a, p->top[k], st);
-      if (r != MRDFT_OK) return r;
+      if (j < p->top_early.size()) {
+        if (per_level) {
+          const cudaError_t e = cudaStreamWaitEvent(st, p->ev_top_cols[j], 0);
+          if (e != cudaSuccess) return join_on_error(cuda_fail(p, e, "cudaStreamWaitEvent(ev_top_cols)"));
+        }
+        r = launch_fwd(p, a, p->top[k], st, 2, early_scr(j));
+      } else {
+        r = launch_fwd(p, a, p->top[k], st);
+      }
+      if (r != MRDFT_OK) return join_on_error(r);
     }
   }
   if (p->flags & MRDFT_FLAG_BITREV) {
@@ -1096,7 +1149,8 @@ mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_
   if (o.adj_cb != 0 && (o.adj_cb < 9 || o.adj_cb > 10))
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: adj_cb must be 0 or in [9, 10]");
   if (!sw(o.fwd_rows_prefetch) || !sw(o.fwd_rows14) || !sw(o.adj_rows13) || !sw(o.dual_cols) || !sw(o.fwd_tree) ||
-      !sw(o.tile_first) || !sw(o.tile_lean) || !sw(o.fwd_rows12) || !sw(o.top_cols_early))
+      !sw(o.tile_first) || !sw(o.tile_lean) || !sw(o.fwd_rows12) || !sw(o.top_cols_early) ||
+      !sw(o.top_overlap))
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: switches must be MRDFT_OPT_DEFAULT, _OFF or _ON");
   if (!lengths) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: lengths is NULL");
   if (batch < 1 || batch > (int64_t(1) << 30))
@@ -1139,6 +1193,7 @@ mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_
   p->tile_lean = on(o.tile_lean, p->tile_lean);
   p->fwd_rows12 = on(o.fwd_rows12, p->fwd_rows12);
   p->top_cols_early = on(o.top_cols_early, p->top_cols_early);
+  p->top_overlap = on(o.top_overlap, p->top_overlap);
   mrdft_status st = build_plan(p, lengths, n_lengths, batch);
   if (st != MRDFT_OK) {
     fail(nullptr, st, p->err);
@@ -1167,6 +1222,7 @@ mrdft_status mrdft_plan_get_opts(mrdft_plan_t p, mrdft_exec_opts* opts) {
   opts->fwd_rows12 = sw(p->fwd_rows12);
   opts->tile_split = p->tile_split;
   opts->top_cols_early = sw(p->top_cols_early);
+  opts->top_overlap = sw(p->top_overlap);
   return MRDFT_OK;
 }
 

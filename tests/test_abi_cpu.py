@@ -105,7 +105,9 @@ def test_api_refuses_cpu_tensors():
 
 @pytest.mark.parametrize("field,value", [("seg_log", 11), ("seg_log", 27), ("streams", 17), ("fwd_cb", 8),
                                          ("fwd_cb", 12), ("adj_cb", 11), ("fwd_rows_prefetch", 3),
-                                         ("dual_cols", -1), ("fwd_tree", 7), ("adj_rows13", 5)])
+                                         ("dual_cols", -1), ("fwd_tree", 7), ("adj_rows13", 5),
+                                         ("tile_lean", 4), ("top_cols_early", 9), ("top_overlap", 3),
+                                         ("tile_split", 65)])
 def test_plan_ex_rejects_bad_options(lib, field, value):
     """Every execution option is range-checked before any device work."""
     from paper_1507_02525_gb300 import _lib
@@ -116,6 +118,16 @@ def test_plan_ex_rejects_bad_options(lib, field, value):
     assert lib.mrdft_plan_ex(ctypes.byref(h), arr, 1, 1, 0, 0, ctypes.byref(o)) == 1
     assert h.value is None
     assert "mrdft_plan_ex" in lib.mrdft_last_error(None).decode()
+
+
+def test_exec_opts_layout_matches_header():
+    """The ctypes mirror of mrdft_exec_opts has the header's fields, in order."""
+    from paper_1507_02525_gb300 import _lib
+    hdr = open(HEADER).read()
+    body = re.search(r"typedef struct \{([^}]*)\} mrdft_exec_opts;", hdr).group(1)
+    fields = re.findall(r"int32_t (\w+);", body)
+    assert fields == [n for n, _ in _lib.ExecOpts._fields_]
+    assert ctypes.sizeof(_lib.ExecOpts) == 4 * len(fields)
 
 
 def test_exec_opts_from_dict():

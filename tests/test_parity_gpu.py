@@ -883,6 +883,33 @@ def test_tile_split_both_directions(oracle, split, seg_log, streams):
         check_adjoint(gxs[s], oracle.adjoint(gys[s].astype(np.complex128)), gys[s], f"split={split} s={s}")
 
 
+@pytest.mark.parametrize("seg_log,streams,early", [(14, 3, False), (16, 1, True), (18, 4, False)])
+def test_top_overlap(oracle, seg_log, streams, early):
+    """top_overlap: the cols passes of the levels above the segment size run on
+    their own stream, each level's rows pass waiting only for its own cols pass
+    (alone: from the end of the segments; with top_cols_early: from the start)
+    -- under graph replay, repeated, every level of every signal."""
+    lengths = [1 << 20, 1 << 17, 1 << 19, 1 << 13]
+    x = inputs.complex_signals(1, sum(lengths), seed=809)[0]
+    plan = _lib.Plan(lengths, len(lengths), graph=True, seg_log=seg_log, streams=streams,
+                     opts={"top_overlap": True, "top_cols_early": early})
+    o = plan.opts()
+    assert o["top_overlap"] is True and o["top_cols_early"] is early
+    xt = torch.from_numpy(x).cuda()
+    y = torch.empty(plan.out_elems, dtype=torch.complex64, device="cuda")
+    s = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        for _ in range(3):
+            y.fill_(float("nan"))
+            plan.forward(xt.data_ptr(), y.data_ptr(), s.cuda_stream)
+    torch.cuda.synchronize()
+    plan.status_poll()
+    ys = split_out(y.cpu().numpy(), lengths)
+    for k, xs in enumerate(split_in(x, lengths)):
+        check_forward_levels(ys[k], oracle.forward(xs.astype(np.complex128)), xs, f"overlap seg={seg_log} s={k}")
+
+
 @pytest.mark.parametrize("seg_log,streams", [(14, 3), (16, 1), (18, 4)])
 def test_top_cols_early(oracle, seg_log, streams):
     """top_cols_early: the cols passes of the levels above the segment size run
