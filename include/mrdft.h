@@ -209,8 +209,13 @@ mrdft_status mrdft_adjoint(mrdft_plan_t plan, const void* gy, void* gx, mrdft_st
  * mrdft_forward_host -- the same transform for HOST buffers: copies x to the
  * plan's device staging buffers on `stream`, runs mrdft_forward, copies y
  * back and synchronises the stream.  x and y are host pointers (pinned
- * memory gives full copy bandwidth).  The first call allocates the staging
- * buffers (MRDFT_ENOMEM on failure).
+ * memory gives full copy bandwidth).  Parts of y that are final early (the
+ * in-tile levels, then the levels inside the segments) start their copy to
+ * the host while the rest is computed, on a copy stream of the plan joined
+ * back to `stream` (up to 64 copies per call; otherwise, and with
+ * MRDFT_FLAG_BITREV, one copy at the end).  This entry point never replays a
+ * graph.  The first call allocates the staging buffers (MRDFT_ENOMEM on
+ * failure).  y must not be read before the call returns.
  */
 mrdft_status mrdft_forward_host(mrdft_plan_t plan, const void* x_host, void* y_host,
                                 mrdft_stream_t stream);

@@ -186,6 +186,18 @@ struct mrdft_plan_s {
   int* d_status = nullptr;
   void* d_stage_x = nullptr;
   void* d_stage_y = nullptr;
+  // mrdft_forward_host: output runs copied to the host as soon as the part
+  // of the forward that writes them is done -- phase 0 after the in-tile
+  // levels (one tile launch), 1 after the segments, 2 at the end -- on a
+  // stream of their own, forked from and joined back to the caller's
+  struct HostRun {
+    int64_t off, count;  // y elements
+  };
+  std::vector<HostRun> host_runs[3];
+  bool host_runs_ready = false;
+  cudaStream_t d2h = nullptr;
+  cudaEvent_t ev_host[4] = {};  // phases 0..2, join
+  void* host_dst = nullptr;     // set only while mrdft_forward_host enqueues
 
 
   std::vector<GraphEntry> fwd_graphs, adj_graphs;
@@ -318,6 +330,12 @@ void release(mrdft_plan_s* p) {
   p->ev_early_go = p->ev_early_done = nullptr;
   for (cudaEvent_t e : p->event_pool) cudaEventDestroy(e);
   p->event_pool.clear();
+  if (p->d2h) cudaStreamDestroy(p->d2h);
+  p->d2h = nullptr;
+  for (cudaEvent_t& e : p->ev_host) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   for (auto& g : p->fwd_graphs) cudaGraphExecDestroy(g.exec);
   for (auto& g : p->adj_graphs) cudaGraphExecDestroy(g.exec);
   p->fwd_graphs.clear();
@@ -759,6 +777,58 @@ mrdft_status run_segments(mrdft_plan_s* p, cudaStream_t st, F&& chain, A&& after
   return r;
 }
 
+// The output runs of mrdft_forward_host by the phase after which they are
+// final: a signal's in-tile levels (all of it when m <= 12) after the tile
+// launch (phase 0, when the in-tile levels of every segment are one launch;
+// tiny signals run before it), levels 13..seg_log after the segments
+// (phase 1), the levels above the segment size at the end (phase 2).  The
+// bit-reversed layout is written at the very end, and too many runs would
+// cost more host calls than they save: then one run at the end.
+void build_host_runs(mrdft_plan_s* p) {
+  for (auto& v : p->host_runs) v.clear();
+  const bool early_tiles = p->tile_first && p->tile_parts.size() <= 1;
+  std::vector<size_t> order(p->sigs.size());
+  for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+  std::sort(order.begin(), order.end(), [&](size_t u, size_t v) { return p->sigs[u].out_off < p->sigs[v].out_off; });
+  auto add = [&](int ph, int64_t off, int64_t cnt) {
+    if (cnt <= 0) return;
+    auto& v = p->host_runs[ph];
+    if (!v.empty() && v.back().off + v.back().count == off) v.back().count += cnt;
+    else v.push_back({off, cnt});
+  };
+  for (size_t k : order) {
+    const SigDesc& sd = p->sigs[k];
+    const int64_t N = int64_t(1) << sd.m;
+    const int tile_lv = std::min(sd.m, kTileLog), seg_lv = std::max(tile_lv, std::min(sd.m, p->seg_log));
+    add(early_tiles ? 0 : 1, sd.out_off, tile_lv * N);
+    add(1, sd.out_off + tile_lv * N, (seg_lv - tile_lv) * N);
+    add(2, sd.out_off + seg_lv * N, (sd.m - seg_lv) * N);
+  }
+  const size_t runs = p->host_runs[0].size() + p->host_runs[1].size() + p->host_runs[2].size();
+  if ((p->flags & MRDFT_FLAG_BITREV) || runs > 64) {
+    for (auto& v : p->host_runs) v.clear();
+    p->host_runs[2].push_back({0, p->out_elems});
+  }
+  p->host_runs_ready = true;
+}
+
+// Enqueue the copies of one phase on the copy stream, after the caller's
+// stream reaches this point; phase 2 also joins the copy stream back.
+mrdft_status host_phase(mrdft_plan_s* p, int ph, const void* y, cudaStream_t st) {
+  const auto& runs = p->host_runs[ph];
+  if (runs.empty() && ph < 2) return MRDFT_OK;
+  MRDFT_CUDA(p, cudaEventRecord(p->ev_host[ph], st));
+  MRDFT_CUDA(p, cudaStreamWaitEvent(p->d2h, p->ev_host[ph], 0));
+  for (const auto& r : runs)
+    MRDFT_CUDA(p, cudaMemcpyAsync(static_cast<float2*>(p->host_dst) + r.off, static_cast<const float2*>(y) + r.off,
+                                  (size_t)r.count * sizeof(float2), cudaMemcpyDeviceToHost, p->d2h));
+  if (ph == 2) {
+    MRDFT_CUDA(p, cudaEventRecord(p->ev_host[3], p->d2h));
+    MRDFT_CUDA(p, cudaStreamWaitEvent(st, p->ev_host[3], 0));
+  }
+  return MRDFT_OK;
+}
+
 mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream_t st) {
   FwdArgs a{};
   a.x = x;
@@ -786,6 +856,10 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
   const bool parts = p->tile_first && p->tile_parts.size() > 1;
   if (p->tile_first && !parts && p->tile_all.count) {
     mrdft_status q = launch_fwd(p, a, p->tile_all, st);
+    if (q != MRDFT_OK) return q;
+  }
+  if (p->host_dst) {
+    mrdft_status q = host_phase(p, 0, y, st);
     if (q != MRDFT_OK) return q;
   }
   if (parts && p->tile_parts[0].count) {
@@ -900,6 +974,10 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
       },
       before, forked);
   if (r != MRDFT_OK) return join_on_error(r);
+  if (p->host_dst) {
+    r = host_phase(p, 1, y, st);
+    if (r != MRDFT_OK) return join_on_error(r);
+  }
   if (early && !early_at_start) {
     r = start_early();
     if (r != MRDFT_OK) return r;
@@ -937,6 +1015,7 @@ mrdft_status enqueue_forward(mrdft_plan_s* p, const void* x, void* y, cudaStream
       MRDFT_CUDA(p, launch_bitrev_big(b, lv.second.second, lv.first, st));
     }
   }
+  if (p->host_dst) return host_phase(p, 2, y, st);
   return MRDFT_OK;
 }
 
@@ -1287,10 +1366,24 @@ mrdft_status mrdft_forward_host(mrdft_plan_t p, const void* x_host, void* y_host
     if (e == cudaSuccess) e = cudaMalloc(&p->d_stage_y, yb);
     if (e != cudaSuccess) return fail(p, MRDFT_ENOMEM, std::string("staging allocation: ") + cudaGetErrorString(e));
   }
+  if (!p->d2h) {
+    MRDFT_CUDA(p, cudaStreamCreateWithFlags(&p->d2h, cudaStreamNonBlocking));
+    for (cudaEvent_t& e : p->ev_host) MRDFT_CUDA(p, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  }
+  if (!p->host_runs_ready) build_host_runs(p);
+  int dev = -1;
+  MRDFT_CUDA(p, cudaGetDevice(&dev));
+  if (dev != p->device) return fail(p, MRDFT_EINVAL, "plan used on a different device than it was created on");
   MRDFT_CUDA(p, cudaMemcpyAsync(p->d_stage_x, x_host, xb, cudaMemcpyHostToDevice, st));
-  mrdft_status s = run(p, p->fwd_graphs, enqueue_forward, p->d_stage_x, p->d_stage_y, st);
-  if (s != MRDFT_OK) return s;
-  MRDFT_CUDA(p, cudaMemcpyAsync(y_host, p->d_stage_y, yb, cudaMemcpyDeviceToHost, st));
+  // enqueued directly (no graph: the copies carry this call's host pointer),
+  // each finished part of the output leaving while the rest is computed
+  p->host_dst = y_host;
+  mrdft_status s = enqueue_forward(p, p->d_stage_x, p->d_stage_y, st);
+  p->host_dst = nullptr;
+  if (s != MRDFT_OK) {
+    cudaStreamSynchronize(p->d2h);
+    return s;
+  }
   MRDFT_CUDA(p, cudaStreamSynchronize(st));
   return MRDFT_OK;
 }

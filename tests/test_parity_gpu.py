@@ -217,6 +217,33 @@ def test_forward_host_entry(oracle):
     np.testing.assert_array_equal(y_host, run_forward(plan, x.reshape(-1)))
 
 
+@pytest.mark.parametrize("case", ["phases", "tile_split", "bitrev", "many_runs"])
+def test_forward_host_overlapped_copies(oracle, case):
+    """mrdft_forward_host copies each finished part of the output (the in-tile
+    levels after the tile launch, the segment levels after the segments, the
+    rest at the end) while the forward goes on; every case must equal the
+    device-buffer forward bit for bit, into pinned and pageable host memory,
+    over repeated calls."""
+    if case == "many_runs":
+        lengths = [1 << int(m) for m in np.random.default_rng(5).integers(3, 15, size=100)]
+    else:
+        lengths = [1 << 20, 1 << 17, 1 << 13, 1 << 5, 1 << 3]
+    opts = {"tile_split": 2} if case == "tile_split" else {}
+    plan = _lib.Plan(lengths, len(lengths), graph=True, seg_log=16, streams=3, opts=opts, bitrev=case == "bitrev")
+    x = inputs.complex_signals(1, sum(lengths), seed=31)[0]
+    want = run_forward(plan, x)
+    xp = torch.from_numpy(x).pin_memory()
+    yp = torch.empty(plan.out_elems, dtype=torch.complex64).pin_memory()
+    for _ in range(2):
+        yp.fill_(float("nan"))
+        plan.forward_host(xp.data_ptr(), yp.data_ptr(), torch.cuda.current_stream().cuda_stream)
+        np.testing.assert_array_equal(yp.numpy(), want)
+    y_pageable = np.full(plan.out_elems, np.nan, dtype=np.complex64)
+    plan.forward_host(x.ctypes.data, y_pageable.ctypes.data, 0)
+    np.testing.assert_array_equal(y_pageable, want)
+    plan.status_poll()
+
+
 def test_forward_api_shapes(oracle):
     x = inputs.complex_signals(2, 256, seed=3)
     y = api.mrdft(torch.from_numpy(x).cuda())
