@@ -251,10 +251,17 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     const AdjTileSig& ts = TS[e >> tl];
     const int off = e & ((1 << tl) - 1);
     adj_chunk_levels_4_1<FUSED>(a, ts, off, P, acc, lsum);
-    float4* dst = reinterpret_cast<float4*>(a.gx + ts.x_base + off);
+    if (it.nsig == 1 && Tn == T) {
+      // a whole single-signal tile: each warp stores its 32 rows of x_bar
+      // through its own rows of ACC (read above by these lanes only)
+      float2* base = a.gx + ts.x_base + ((chunk & ~31) << 4);
+      warp_rows16_store(acc, ACC + ((tid >> 5) << 9), [&](int r) MRDFT_INL { return base + (r << 4); });
+    } else {
+      float4* dst = reinterpret_cast<float4*>(a.gx + ts.x_base + off);
 #pragma unroll
-    for (int q = 0; q < 8; ++q)
-      __stcs(dst + q, make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y));
+      for (int q = 0; q < 8; ++q)
+        __stcs(dst + q, make_float4(acc[2 * q].x, acc[2 * q].y, acc[2 * q + 1].x, acc[2 * q + 1].y));
+    }
   }
   loss_flush<FUSED>(a, lsum);
 }

@@ -211,6 +211,49 @@ __device__ __forceinline__ void st_l2_keep(float2* p, float2 v, uint64_t pol) {
                : "memory");
 }
 
+// Rows of 16 complex values (128 bytes), one row per thread of a warp,
+// moved between registers and global memory so that every global access
+// instruction covers 512 contiguous bytes instead of 16 bytes in each of 32
+// lines: the warp's 32 rows pass through its own 4 KB of shared memory
+// (`slice`, 16-byte aligned), 16-byte chunks XOR-swizzled by row, which is
+// conflict-free both ways.  Chunk c = lane + 32 t of the transfer is chunk
+// c & 7 of row c >> 3 of the warp.  Every lane of the warp calls.
+//   store: row_ptr(r) = global address of row r (r < 32), 16-byte aligned
+//   load:  chunk(r, q) = the float4 q (< 8) of row r, read from global memory
+template <class RowPtr>
+__device__ __forceinline__ void warp_rows16_store(const float2 (&v)[16], float2* slice, RowPtr&& row_ptr) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int q = 0; q < 8; ++q)
+    *reinterpret_cast<float4*>(slice + (lane << 4) + ((q ^ (lane & 7)) << 1)) =
+        make_float4(v[2 * q].x, v[2 * q].y, v[2 * q + 1].x, v[2 * q + 1].y);
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int c = lane + 32 * t, r = c >> 3;
+    __stcs(reinterpret_cast<float4*>(row_ptr(r)) + (c & 7),
+           *reinterpret_cast<const float4*>(slice + (r << 4) + (((c & 7) ^ (r & 7)) << 1)));
+  }
+  __syncwarp();
+}
+template <class Chunk>
+__device__ __forceinline__ void warp_rows16_load(float2 (&v)[16], float2* slice, Chunk&& chunk) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int c = lane + 32 * t, r = c >> 3;
+    *reinterpret_cast<float4*>(slice + (r << 4) + (((c & 7) ^ (r & 7)) << 1)) = chunk(r, c & 7);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float4 x = *reinterpret_cast<const float4*>(slice + (lane << 4) + ((q ^ (lane & 7)) << 1));
+    v[2 * q] = make_float2(x.x, x.y);
+    v[2 * q + 1] = make_float2(x.z, x.w);
+  }
+  __syncwarp();
+}
+
 // Invalidate one 128-byte L2 line without writing it back (dead scratch).
 // p must be 128-byte aligned.
 __device__ __forceinline__ void discard_l2(const void* p) {

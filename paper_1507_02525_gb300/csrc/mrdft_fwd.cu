@@ -64,10 +64,12 @@ static_assert(sizeof(TileSig) == 24, "TileSig layout");
 
 // Levels 1..4 of one 16-sample chunk (one 128-byte row of the tile), in
 // registers: A^(1), then U / V / D / F per level with compile-time twiddles.
-// Every level is stored straight to global memory (the thread writes whole
-// 128-byte lines); level 4 also goes to shared memory for level 5.
-__device__ __forceinline__ void tile_chunk_levels_1_4(const FwdArgs& a, const float2* X, float2* B4,
-                                                      int chunk, const TileSig& ts, int off) {
+// Every level goes to global memory -- with `slice` (a whole single-signal
+// tile) through the warp's own shared memory so that the stores coalesce
+// (warp_rows16_store), else row by row; level 4 also goes to shared memory
+// for level 5.
+__device__ __forceinline__ void tile_chunk_levels_1_4(const FwdArgs& a, const float2* X, float2* B4, int chunk,
+                                                      const TileSig* TS, int tl, float2* slice) {
   float2 xr[16], yr[16];
 #pragma unroll
   for (int q = 0; q < 8; ++q) {
@@ -75,16 +77,25 @@ __device__ __forceinline__ void tile_chunk_levels_1_4(const FwdArgs& a, const fl
     xr[2 * q] = make_float2(v.x, v.y);
     xr[2 * q + 1] = make_float2(v.z, v.w);
   }
-  float2* yl = a.y + ts.out_base + off;
-  const int64_t lstride = (int64_t)1 << ts.m;
+  const int e = chunk << 4, wrow0 = (chunk & ~31) << 4;  // this row, the warp's first row
+  auto store_level = [&](int j) MRDFT_INL {
+    if (slice) {
+      float2* base = a.y + TS[0].out_base + ((int64_t)(j - 1) << TS[0].m) + wrow0;
+      warp_rows16_store(yr, slice, [&](int r) MRDFT_INL { return base + (r << 4); });
+    } else {
+      const TileSig& t = TS[e >> tl];
+      float4* dst = reinterpret_cast<float4*>(a.y + t.out_base + ((int64_t)(j - 1) << t.m) + (e & ((1 << tl) - 1)));
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        __stcs(dst + q, make_float4(yr[2 * q].x, yr[2 * q].y, yr[2 * q + 1].x, yr[2 * q + 1].y));
+    }
+  };
 #pragma unroll
   for (int w = 0; w < 8; ++w) {
     yr[2 * w] = cadd(xr[2 * w], xr[2 * w + 1]);
     yr[2 * w + 1] = csub(xr[2 * w], xr[2 * w + 1]);
   }
-#pragma unroll
-  for (int q = 0; q < 8; ++q)
-    __stcs(reinterpret_cast<float4*>(yl) + q, make_float4(yr[2 * q].x, yr[2 * q].y, yr[2 * q + 1].x, yr[2 * q + 1].y));
+  store_level(1);
   static_for<2, 5>([&](auto J) MRDFT_INL {
     constexpr int j = decltype(J)::value;
     constexpr int L = 1 << j, h = L / 2;
@@ -108,10 +119,7 @@ __device__ __forceinline__ void tile_chunk_levels_1_4(const FwdArgs& a, const fl
         yr[w * L + 2 * k + 1] = z[k];
       });
     });
-    float4* dst = reinterpret_cast<float4*>(yl + (j - 1) * lstride);
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-      __stcs(dst + q, make_float4(yr[2 * q].x, yr[2 * q].y, yr[2 * q + 1].x, yr[2 * q + 1].y));
+    store_level(j);
   });
 #pragma unroll
   for (int q = 0; q < 8; ++q)
@@ -188,10 +196,13 @@ __global__ void __launch_bounds__(NT, LEAN ? 3 : (NT <= 256 ? 2 : 1)) k_fwd_tile
   }
   __syncthreads();
 
-  // ---- levels 1..4 in registers, one 16-sample chunk per thread
+  // ---- levels 1..4 in registers, one 16-sample chunk per thread; a whole
+  // single-signal tile stores them through each warp's own part of B (the
+  // rows its level 4 takes there, written after the staged stores)
   {
     const int e = tid << 4;
-    if (e < Tn) tile_chunk_levels_1_4(a, X, B, tid, TS[e >> tl], e & ((1 << tl) - 1));
+    float2* slice = (it.nsig == 1 && Tn == T) ? B + pad16((tid >> 5) << 9) : nullptr;
+    if (e < Tn) tile_chunk_levels_1_4(a, X, B, tid, TS, tl, slice);
   }
   __syncthreads();
 
