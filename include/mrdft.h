@@ -150,6 +150,11 @@ mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t 
  *              its own scratch, and each level's rows pass waits only for
  *              its own cols pass: the cols pass of a level overlaps the rows
  *              pass of the level below (default off)
+ *   levels_parallel : a plan of ONE signal of 2^5..2^12 samples computes
+ *              each level from x in a CTA of its own (both halves of every
+ *              window by FFT), all levels at once, instead of the in-tile
+ *              recursion, whose chain of dependent levels sets the latency of
+ *              a signal this small (default on; forward only)
  */
 #define MRDFT_OPT_DEFAULT 0
 #define MRDFT_OPT_OFF 1
@@ -170,6 +175,7 @@ typedef struct {
   int32_t tile_split;
   int32_t top_cols_early;
   int32_t top_overlap;
+  int32_t levels_parallel;
 } mrdft_exec_opts;
 
 /*

@@ -47,9 +47,9 @@ class ExecOpts(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int32) for n in ("seg_log", "streams", "fwd_cb", "adj_cb", "fwd_rows_prefetch",
                                                "fwd_rows14", "adj_rows13", "dual_cols", "fwd_tree", "tile_first",
                                                "tile_lean", "fwd_rows12", "tile_split", "top_cols_early",
-                                               "top_overlap")]
+                                               "top_overlap", "levels_parallel")]
     SWITCHES = ("fwd_rows_prefetch", "fwd_rows14", "adj_rows13", "dual_cols", "fwd_tree", "tile_first", "tile_lean",
-                "fwd_rows12", "top_cols_early", "top_overlap")
+                "fwd_rows12", "top_cols_early", "top_overlap", "levels_parallel")
 
     @classmethod
     def from_dict(cls, d):

@@ -275,6 +275,60 @@ __global__ void __launch_bounds__(NT, LEAN ? 3 : (NT <= 256 ? 2 : 1)) k_fwd_tile
   });
 }
 
+// ============================================================ lone signal
+
+// One signal of N = 2^m samples, 2^5 <= N <= 2^12, alone in its plan: one
+// CTA per level, level i from x alone.  Both halves of every window come from
+// an FFT of length h: the even bins are the DFT of the folded window a + b
+// (Eq. 2 unrolled down to x), the odd bins the DFT of (a - b) w^n (Eq. 3, D,
+// F), so the m levels run side by side instead of one after another -- the
+// in-tile recursion is a chain of a dozen dependent steps, and a signal this
+// small is bound by that chain's latency, not by throughput.
+constexpr int kLevelsThreads = 512;
+constexpr size_t levels_smem() { return (size_t)(2 * kTile + twq_size(kTileLog)) * sizeof(float2); }
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_fwd_levels(const FwdArgs a) {
+  constexpr int T = kTile;
+  extern __shared__ __align__(1024) float2 sm[];
+  float2* X = sm;           // x (swz128)
+  float2* Z = sm + T;       // FFT work area
+  float2* TQ = sm + 2 * T;  // quarter-wave w_{2^12}
+  const int tid = threadIdx.x;
+  const int id = a.nids > 0 ? a.sig_ids[0] : -1;
+  if (id < 0 || id >= a.nsigs || a.sigs[id].m < 5 || a.sigs[id].m > kTileLog) {
+    if (tid == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
+  const SigDesc sd = a.sigs[id];
+  const int m = sd.m, N = 1 << m;
+  const int i = (int)blockIdx.x + 1;  // the level of this CTA (grid = m)
+  if (i > m) return;
+#pragma unroll 4
+  for (int c = tid; c < (N >> 1); c += NT) st4s(X + swz128(2 * c), load_x2(a, sd.in_off + 2 * c));
+  load_twq<NT>(TQ, kTileLog, a.tw);
+  __syncthreads();
+  float2* ylev = a.y + sd.out_off + ((int64_t)(i - 1) << m);
+  if (i == 1) {  // A^(1)
+    for (int c = tid; c < (N >> 1); c += NT) {
+      const float2 x0 = X[swz128(2 * c)], x1 = X[swz128(2 * c + 1)];
+      const float2 s0 = cadd(x0, x1), s1 = csub(x0, x1);
+      __stcs(reinterpret_cast<float4*>(ylev) + c, make_float4(s0.x, s0.y, s1.x, s1.y));
+    }
+    return;
+  }
+  const TwQ tw{TQ, kTileLog};
+  const int h = 1 << (i - 1);
+  // sequence s = 2 w + c of window w: c = 0 the folded window, 1 the twiddled
+  // half-difference; its bin k is bin 2k + c of the window
+  auto src = [&](int s, int n) MRDFT_INL -> float2 {
+    const int base = (s >> 1) << i;
+    const float2 xa = X[swz128(base + n)], xb = X[swz128(base + h + n)];
+    return (s & 1) ? cmul(csub(xa, xb), twq_l(tw, i, n)) : cadd(xa, xb);
+  };
+  auto sink = [&](int, int s, int k, float2 v) MRDFT_INL { __stcs(ylev + ((s >> 1) << i) + 2 * k + (s & 1), v); };
+  cg_fft<1, kTileLog - 1, NT, T / NT, false, kPreNone>(Z, i - 1, m - i + 1, tw, src, NoPre{}, sink);
+}
+
 // ===================================================================== tiny
 
 // Signals with N <= 16: Eq. 1 term by term, one thread per output bin.
@@ -748,6 +802,9 @@ cudaError_t set_fwd_attributes() {
     e = cudaFuncSetAttribute(k_fwd_tile<kTileLog, kTileThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)tile_smem<true>());
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fwd_levels<kLevelsThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)levels_smem());
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fwd_window<12>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_fwd_window<13>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWinSmem);
@@ -778,6 +835,10 @@ cudaError_t launch_fwd_tile(const FwdArgs& a, int grid, cudaStream_t s) {
     k_fwd_tile<kTileLog, kTileThreads, true><<<grid, kTileThreads, tile_smem<true>(), s>>>(a);
   else
     k_fwd_tile<kTileLog, kTileThreads, false><<<grid, kTileThreads, tile_smem<false>(), s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_fwd_levels(const FwdArgs& a, int m, cudaStream_t s) {
+  k_fwd_levels<kLevelsThreads><<<m, kLevelsThreads, levels_smem(), s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_fwd_tiny(const FwdArgs& a, int nsig_tiny, cudaStream_t s) {

@@ -147,6 +147,8 @@ __device__ __forceinline__ bool tile_sig_ok(const SigDesc* sigs, int nsigs, int 
 // launchers (defined in the .cu files)
 cudaError_t launch_fwd_tile(const FwdArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_fwd_tiny(const FwdArgs& a, int nsig_tiny, cudaStream_t s);
+// one signal of 2^5 .. 2^12 samples alone in its plan: one CTA per level (grid m)
+cudaError_t launch_fwd_levels(const FwdArgs& a, int m, cudaStream_t s);
 cudaError_t launch_fwd_window(const FwdArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_fwd_cols(const FwdArgs& a, int grid, cudaStream_t s);
 // cols passes of levels a.level - 1 and a.level in one read of x; grid =

@@ -146,6 +146,10 @@ struct mrdft_plan_s {
   // of the segments unless top_cols_early), each level's rows pass waiting
   // only for its own cols pass (one event per level)
   bool top_overlap = false;
+  // levels_parallel: a plan of one signal of 2^5..2^12 samples runs its
+  // in-tile launch as one CTA per level (k_fwd_levels); lone_m = that m, else 0
+  bool levels_parallel = true;
+  int lone_m = 0;
   float2* d_scratch_top = nullptr;  // half_elems per early level
   std::vector<int> top_early;       // index into `top` of each early level (its scratch slot follows)
   cudaStream_t early = nullptr;
@@ -600,6 +604,10 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
   }
   p->n_tiles = (int)tiles.size();
   p->n_tile_ids = (int)tile_ids.size();
+  p->lone_m = 0;
+  if (p->levels_parallel && p->nsig == 1 && p->sigs[0].m >= 5 && p->sigs[0].m <= kTileLog && p->n_tiles == 1 &&
+      !tile_ids.empty() && tile_ids[0] == 0)
+    p->lone_m = p->sigs[0].m;
   p->n_level_items = (int64_t)litems.size();
   std::vector<LevelItem> br;
   if (p->flags & MRDFT_FLAG_BITREV) {
@@ -700,7 +708,10 @@ mrdft_status launch_fwd(mrdft_plan_s* p, FwdArgs a, const Launch& L, cudaStream_
     a.sig_ids = p->d_tile_ids;
     a.nids = p->n_tile_ids;
     a.items = p->d_tiles + L.off;
-    MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_TILE, L.bytes, st, [&] { return launch_fwd_tile(a, L.count, st); }));
+    if (p->lone_m)
+      MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_TILE, L.bytes, st, [&] { return launch_fwd_levels(a, p->lone_m, st); }));
+    else
+      MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_TILE, L.bytes, st, [&] { return launch_fwd_tile(a, L.count, st); }));
   } else if (L.kind == LK_WIN) {
     a.items = p->d_levels + L.off;
     MRDFT_CUDA(p, timed(p, MRDFT_KIND_FWD_WINDOW, L.bytes, st, [&] { return launch_fwd_window(a, L.count, st); }));
@@ -1229,7 +1240,7 @@ mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: adj_cb must be 0 or in [9, 10]");
   if (!sw(o.fwd_rows_prefetch) || !sw(o.fwd_rows14) || !sw(o.adj_rows13) || !sw(o.dual_cols) || !sw(o.fwd_tree) ||
       !sw(o.tile_first) || !sw(o.tile_lean) || !sw(o.fwd_rows12) || !sw(o.top_cols_early) ||
-      !sw(o.top_overlap))
+      !sw(o.top_overlap) || !sw(o.levels_parallel))
     return fail(nullptr, MRDFT_EINVAL, "mrdft_plan_ex: switches must be MRDFT_OPT_DEFAULT, _OFF or _ON");
   if (!lengths) return fail(nullptr, MRDFT_EINVAL, "mrdft_plan: lengths is NULL");
   if (batch < 1 || batch > (int64_t(1) << 30))
@@ -1273,6 +1284,7 @@ mrdft_status mrdft_plan_ex(mrdft_plan_t* out, const int64_t* lengths, int64_t n_
   p->fwd_rows12 = on(o.fwd_rows12, p->fwd_rows12);
   p->top_cols_early = on(o.top_cols_early, p->top_cols_early);
   p->top_overlap = on(o.top_overlap, p->top_overlap);
+  p->levels_parallel = on(o.levels_parallel, p->levels_parallel);
   mrdft_status st = build_plan(p, lengths, n_lengths, batch);
   if (st != MRDFT_OK) {
     fail(nullptr, st, p->err);
@@ -1302,6 +1314,7 @@ mrdft_status mrdft_plan_get_opts(mrdft_plan_t p, mrdft_exec_opts* opts) {
   opts->tile_split = p->tile_split;
   opts->top_cols_early = sw(p->top_cols_early);
   opts->top_overlap = sw(p->top_overlap);
+  opts->levels_parallel = sw(p->levels_parallel);
   return MRDFT_OK;
 }
 

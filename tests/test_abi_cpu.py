@@ -107,7 +107,7 @@ def test_api_refuses_cpu_tensors():
                                          ("fwd_cb", 12), ("adj_cb", 11), ("fwd_rows_prefetch", 3),
                                          ("dual_cols", -1), ("fwd_tree", 7), ("adj_rows13", 5),
                                          ("tile_lean", 4), ("top_cols_early", 9), ("top_overlap", 3),
-                                         ("tile_split", 65)])
+                                         ("tile_split", 65), ("levels_parallel", 4)])
 def test_plan_ex_rejects_bad_options(lib, field, value):
     """Every execution option is range-checked before any device work."""
     from paper_1507_02525_gb300 import _lib

@@ -73,6 +73,27 @@ def test_forward_single(oracle, m):
     check_forward_levels(y, ref, x, f"N=2^{m}")
 
 
+@pytest.mark.parametrize("m", [5, 6, 7, 9, 11, 12])
+@pytest.mark.parametrize("real", [False, True])
+def test_forward_lone_signal_levels_parallel(oracle, m, real):
+    """A plan of one signal of 2^5..2^12 samples computes every level in a CTA
+    of its own (levels_parallel, the default); with the option off it runs
+    the in-tile recursion. Both against the oracle, and the default path bit
+    for bit the same on a second call and under graph replay."""
+    N = 1 << m
+    x = (inputs.real_signals(1, N, seed=70 + m) if real else inputs.complex_signals(1, N, seed=70 + m))[0]
+    ref = oracle.forward(x.astype(np.complex128))
+    ys = []
+    for opts, graph in (({}, False), ({}, True), ({"levels_parallel": False}, False)):
+        plan = _lib.Plan([N], 1, real_input=real, graph=graph, opts=opts)
+        assert plan.opts()["levels_parallel"] is (opts.get("levels_parallel", True))
+        y = run_forward(plan, x)
+        np.testing.assert_array_equal(y, run_forward(plan, x))
+        check_forward_levels(y.reshape(m, N), ref, x, f"lone N=2^{m} {opts}")
+        ys.append(y)
+    np.testing.assert_array_equal(ys[0], ys[1])
+
+
 @pytest.mark.parametrize("m", [5, 8, 12, 13, 15])
 def test_forward_real_input(oracle, m):
     N = 1 << m
