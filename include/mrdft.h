@@ -154,7 +154,9 @@ mrdft_status mrdft_plan_opts(mrdft_plan_t* out, const int64_t* lengths, int64_t 
  *              each level from x in a CTA of its own (both halves of every
  *              window by FFT), all levels at once, instead of the in-tile
  *              recursion, whose chain of dependent levels sets the latency of
- *              a signal this small (default on; forward only)
+ *              a signal this small; its adjoint (without the fused loss) takes
+ *              each level's share of x_bar in a CTA of its own and adds them
+ *              in level order (default on)
  */
 #define MRDFT_OPT_DEFAULT 0
 #define MRDFT_OPT_OFF 1

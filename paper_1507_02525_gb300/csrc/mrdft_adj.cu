@@ -266,6 +266,74 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
   loss_flush<FUSED>(a, lsum);
 }
 
+// ============================================================ lone signal
+
+// The adjoint of the forward's lone-signal path: one signal of 2^5..2^12
+// samples alone in its plan, one CTA per level.  Level i's share of x_bar is
+// the conjugate transpose of its per-window DFTs, an unnormalised inverse DFT
+// of length 2^i of every window's upstream gradient (computed as the
+// conjugate of the DFT of the conjugate), independent of the other levels;
+// each CTA writes its share to the scratch and the CTA that finishes last
+// adds the m shares in level order (the same sum on every call).
+constexpr int kLevelsThreads = 512;
+constexpr size_t adj_levels_smem() { return (size_t)(2 * kTile + twq_size(kTileLog)) * sizeof(float2); }
+template <int NT>
+__global__ void __launch_bounds__(NT, 1) k_adj_levels(const AdjArgs a) {
+  constexpr int T = kTile;
+  extern __shared__ __align__(1024) float2 sm[];
+  float2* G = sm;           // conj of the level's upstream gradient (swz128)
+  float2* Z = sm + T;       // FFT work area
+  float2* TQ = sm + 2 * T;  // quarter-wave w_{2^12}
+  const int tid = threadIdx.x;
+  const int id = a.nids > 0 ? a.sig_ids[0] : -1;
+  if (id < 0 || id >= a.nsigs || a.sigs[id].m < 5 || a.sigs[id].m > kTileLog || (int)gridDim.x != a.sigs[id].m) {
+    if (tid == 0) set_status(a.status, kStatusBadItem);
+    return;
+  }
+  const SigDesc sd = a.sigs[id];
+  const int m = sd.m, N = 1 << m;
+  const int i = (int)blockIdx.x + 1;
+  float2* C = a.scratch + (int64_t)(i - 1) * N;  // this level's share of x_bar
+  const float4* gl = reinterpret_cast<const float4*>(a.gy + sd.out_off + ((int64_t)(i - 1) << m));
+#pragma unroll 4
+  for (int c = tid; c < (N >> 1); c += NT) {
+    const float4 g = __ldcs(gl + c);
+    st4s_a(G + swz128(2 * c), make_float4(g.x, -g.y, g.z, -g.w));
+  }
+  load_twq<NT>(TQ, kTileLog, a.tw);
+  __syncthreads();
+  if (i == 1) {  // H_2 is its own conjugate transpose
+    for (int c = tid; c < (N >> 1); c += NT) {
+      const float2 g0 = conjf2(G[swz128(2 * c)]), g1 = conjf2(G[swz128(2 * c + 1)]);
+      const float2 s0 = cadd(g0, g1), s1 = csub(g0, g1);
+      *reinterpret_cast<float4*>(C + 2 * c) = make_float4(s0.x, s0.y, s1.x, s1.y);
+    }
+  } else {
+    const TwQ tw{TQ, kTileLog};
+    auto src = [&](int w, int k) MRDFT_INL -> float2 { return G[swz128((w << i) + k)]; };
+    auto sink = [&](int, int w, int n, float2 v) MRDFT_INL { C[(w << i) + n] = conjf2(v); };
+    cg_fft<1, kTileLog, NT, T / NT, false, kPreNone>(Z, i, m - i, tw, src, NoPre{}, sink);
+  }
+  // the last CTA to finish adds the shares, level by level
+  __threadfence();
+  __syncthreads();
+  __shared__ int last;
+  if (tid == 0) last = atomicAdd(a.ticket, 1) == m - 1;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  float4* gx = reinterpret_cast<float4*>(a.gx + sd.in_off);
+  for (int c = tid; c < (N >> 1); c += NT) {
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int l = 0; l < m; ++l) {
+      const float4 v = __ldcg(reinterpret_cast<const float4*>(a.scratch + (int64_t)l * N) + c);
+      s = make_float4(s.x + v.x, s.y + v.y, s.z + v.z, s.w + v.w);
+    }
+    __stcs(gx + c, s);
+  }
+  if (tid == 0) *a.ticket = 0;  // ready for the next launch
+}
+
 // ===================================================================== tiny
 
 // Signals with N <= 16: conjugate transpose of Eq. 1 term by term.
@@ -753,6 +821,9 @@ cudaError_t set_adj_attributes() {
     e = cudaFuncSetAttribute(k_adj_tile<kTileLog, kTileThreads, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjTileSmem);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_adj_levels<kLevelsThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)adj_levels_smem());
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_adj_window<12, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_adj_window<12, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAdjWinSmem);
@@ -783,6 +854,10 @@ cudaError_t launch_adj_tile(const AdjArgs& a, int grid, cudaStream_t s) {
     k_adj_tile<kTileLog, kTileThreads, true><<<grid, kTileThreads, kAdjTileSmem, s>>>(a);
   else
     k_adj_tile<kTileLog, kTileThreads, false><<<grid, kTileThreads, kAdjTileSmem, s>>>(a);
+  return cudaGetLastError();
+}
+cudaError_t launch_adj_levels(const AdjArgs& a, int m, cudaStream_t s) {
+  k_adj_levels<kLevelsThreads><<<m, kLevelsThreads, adj_levels_smem(), s>>>(a);
   return cudaGetLastError();
 }
 cudaError_t launch_adj_tiny(const AdjArgs& a, int nsig_tiny, cudaStream_t s) {

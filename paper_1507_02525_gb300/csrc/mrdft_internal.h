@@ -110,6 +110,9 @@ struct AdjArgs {
   // is added to *loss (which may be nullptr)
   const float2* t;
   double* loss;
+  // lone small signal (launch_adj_levels): the CTAs' finish counter, zero
+  // between launches
+  int* ticket;
 };
 
 // ---- work-item checks
@@ -164,6 +167,10 @@ cudaError_t launch_bitrev_big(const FwdArgs& a, int grid, int level, cudaStream_
 
 cudaError_t launch_adj_tile(const AdjArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_adj_tiny(const AdjArgs& a, int nsig_tiny, cudaStream_t s);
+// one signal of 2^5 .. 2^12 samples alone in its plan, no fused loss: one CTA
+// per level (grid m), each level's x_bar share in a.scratch (m N), summed by
+// the CTA that finishes last
+cudaError_t launch_adj_levels(const AdjArgs& a, int m, cudaStream_t s);
 cudaError_t launch_adj_window(const AdjArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_adj_rows(const AdjArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_adj_cols(const AdjArgs& a, int grid, cudaStream_t s);

@@ -150,6 +150,8 @@ struct mrdft_plan_s {
   // in-tile launch as one CTA per level (k_fwd_levels); lone_m = that m, else 0
   bool levels_parallel = true;
   int lone_m = 0;
+  float2* d_lone = nullptr;  // adjoint: each level's share of x_bar (lone_m x N)
+  int* d_ticket = nullptr;   // adjoint: finish counter of its CTAs
   float2* d_scratch_top = nullptr;  // half_elems per early level
   std::vector<int> top_early;       // index into `top` of each early level (its scratch slot follows)
   cudaStream_t early = nullptr;
@@ -346,7 +348,8 @@ void release(mrdft_plan_s* p) {
   p->adj_graphs.clear();
   void* ptrs[] = {p->d_sigs, p->d_tile_ids, p->d_tiles, p->d_tiny_ids, p->d_levels, p->d_br,
                   p->d_tw13, p->d_twlo, p->d_twhi, p->d_scratch, p->d_e0,
-                  p->d_e1, p->d_etop, p->d_acc, p->d_status, p->d_stage_x, p->d_stage_y, p->d_scratch_top};
+                  p->d_e1, p->d_etop, p->d_acc, p->d_status, p->d_stage_x, p->d_stage_y, p->d_scratch_top,
+                  p->d_lone, p->d_ticket};
   for (void* q : ptrs)
     if (q) cudaFree(q);
 }
@@ -689,6 +692,12 @@ mrdft_status build_plan(mrdft_plan_s* p, const int64_t* lengths, int64_t n_lengt
     if (e == cudaSuccess) e = cudaMalloc(&p->d_acc, 2 * half);
     if (e == cudaSuccess && !p->top_early.empty()) e = cudaMalloc(&p->d_scratch_top, p->top_early.size() * half);
     if (e != cudaSuccess) return fail(p, MRDFT_ENOMEM, std::string("scratch allocation: ") + cudaGetErrorString(e));
+  }
+  if (p->lone_m) {
+    cudaError_t e = cudaMalloc(&p->d_lone, (size_t)p->lone_m * ((size_t)1 << p->lone_m) * sizeof(float2));
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_ticket, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_ticket, 0, sizeof(int));
+    if (e != cudaSuccess) return fail(p, MRDFT_ENOMEM, std::string("lone-signal scratch: ") + cudaGetErrorString(e));
   }
   MRDFT_CUDA(p, cudaMalloc(&p->d_status, sizeof(int)));
   MRDFT_CUDA(p, cudaMemset(p->d_status, 0, sizeof(int)));
@@ -1043,7 +1052,13 @@ mrdft_status launch_adj(mrdft_plan_s* p, AdjArgs a, const Launch& L, cudaStream_
     a.nids = p->n_tile_ids;
     a.items = p->d_tiles + L.off;
     a.e_in = (!in_top && S == kTileLog && p->d_etop) ? p->d_etop : ebuf(kTileLog + 1);
-    MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_TILE, L.bytes, st, [&] { return launch_adj_tile(a, L.count, st); }));
+    if (p->lone_m && !a.t) {
+      a.scratch = p->d_lone;
+      a.ticket = p->d_ticket;
+      MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_TILE, L.bytes, st, [&] { return launch_adj_levels(a, p->lone_m, st); }));
+    } else {
+      MRDFT_CUDA(p, timed(p, MRDFT_KIND_ADJ_TILE, L.bytes, st, [&] { return launch_adj_tile(a, L.count, st); }));
+    }
     return MRDFT_OK;
   }
   a.items = p->d_levels + L.off;

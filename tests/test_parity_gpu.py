@@ -94,6 +94,26 @@ def test_forward_lone_signal_levels_parallel(oracle, m, real):
     np.testing.assert_array_equal(ys[0], ys[1])
 
 
+@pytest.mark.parametrize("m", [5, 6, 8, 10, 12])
+def test_adjoint_lone_signal_levels_parallel(oracle, m):
+    """The adjoint of a lone 2^5..2^12 signal: every level's share of x_bar in
+    a CTA of its own, summed by the last CTA to finish -- against the oracle's
+    adjoint, bit for bit the same on repeated calls and under graph replay, and
+    against the in-tile path (levels_parallel off)."""
+    N = 1 << m
+    gy = inputs.targets(1, N, seed=90 + m)[0]  # [m, N]
+    ref = oracle.adjoint(gy.astype(np.complex128))
+    outs = []
+    for opts, graph in (({}, False), ({}, True), ({"levels_parallel": False}, False)):
+        plan = _lib.Plan([N], 1, graph=graph, opts=opts)
+        gx = run_adjoint(plan, gy.reshape(-1))
+        for _ in range(2):
+            np.testing.assert_array_equal(gx, run_adjoint(plan, gy.reshape(-1)))
+        check_adjoint(gx, ref, gy, f"lone N=2^{m} {opts}")
+        outs.append(gx)
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
 @pytest.mark.parametrize("m", [5, 8, 12, 13, 15])
 def test_forward_real_input(oracle, m):
     N = 1 << m
