@@ -130,9 +130,10 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
   constexpr int T = 1 << TLOG;
   static_assert(T == 16 * NT, "tile = 16 samples per thread");
   extern __shared__ __align__(1024) float2 sm[];
-  float2* ACC = sm;                        // T, x_bar accumulator (swz128)
-  float2* E[2] = {sm + T, sm + T + T / 2}; // even-bin propagation, level i in E[i & 1]
-  float2* Z = sm + 2 * T;                  // T/2 (staging, then zlay), odd-bin inverse DFT work
+  constexpr int TA = pad16_size(T);
+  float2* ACC = sm;                          // x_bar accumulator (pad16)
+  float2* E[2] = {sm + TA, sm + TA + T / 2}; // even-bin propagation, level i in E[i & 1]
+  float2* Z = sm + TA + T;                   // T/2 (staging, then zlay), odd-bin inverse DFT work
   float2* TQ = Z + T / 2;                  // quarter-wave w_{2^TLOG} (padded)
   AdjTileSig* TS = reinterpret_cast<AdjTileSig*>(TQ + twq_size(TLOG));
   const int tid = threadIdx.x;
@@ -173,7 +174,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     const int e = c << 1;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
     if (below) v = __ldcg(reinterpret_cast<const float4*>(a.acc + 2 * sd0.aux_off + ((int64_t)it.tile << tl) + e));
-    st4s_a(ACC + swz128(e), v);
+    st4s_a(ACC + pad16(e), v);
   }
 
   // ---- levels tl .. 5 through shared memory
@@ -230,7 +231,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     auto sink = [&](int, int b, int n, float2 v) MRDFT_INL {
       const float2 c = cmulc(conjf2(v), twq_l(tw, i, n));  // conj(w^n) zb[n]
       const int base = b << i;
-      const int i0 = swz128(base + n), i1 = swz128(base + h + n);
+      const int i0 = pad16(base + n), i1 = pad16(base + h + n);
       ACC[i0] = cadd(ACC[i0], c);
       ACC[i1] = csub(ACC[i1], c);
     };
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     float2 P[16], acc[16];
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      acc[q] = ACC[swz128(e + q)];
+      acc[q] = ACC[pad16(e + q)];
       P[q] = E[1][swzf(((chunk >> 1) << 4) + q)];  // E_5 of the level-5 parent
     }
     const AdjTileSig& ts = TS[e >> tl];
@@ -255,7 +256,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
       // a whole single-signal tile: each warp stores its 32 rows of x_bar
       // through its own rows of ACC (read above by these lanes only)
       float2* base = a.gx + ts.x_base + ((chunk & ~31) << 4);
-      warp_rows16_store(acc, ACC + ((tid >> 5) << 9), [&](int r) MRDFT_INL { return base + (r << 4); });
+      warp_rows16_store(acc, ACC + pad16((tid >> 5) << 9), [&](int r) MRDFT_INL { return base + (r << 4); });
     } else {
       float4* dst = reinterpret_cast<float4*>(a.gx + ts.x_base + off);
 #pragma unroll
@@ -812,7 +813,8 @@ cudaError_t adj_rows_attr() {
 // ================================================================ launchers
 
 static constexpr size_t kAdjTileSmem =
-    (size_t)(2 * kTile + kTile / 2 + twq_size(kTileLog)) * sizeof(float2) + kAdjMaxPack * sizeof(AdjTileSig);
+    (size_t)(pad16_size(kTile) + kTile + kTile / 2 + twq_size(kTileLog)) * sizeof(float2) +
+    kAdjMaxPack * sizeof(AdjTileSig);
 static constexpr size_t kAdjWinSmem = (size_t)((1 << kWinMaxLog) + twq_size(13)) * sizeof(float2);
 cudaError_t set_adj_attributes() {
   cudaError_t e = cudaFuncSetAttribute(k_adj_tile<kTileLog, kTileThreads, true>,
