@@ -758,11 +758,15 @@ mrdft_status launch_fwd(mrdft_plan_s* p, FwdArgs a, const Launch& L, cudaStream_
 struct NoAfter {
   mrdft_status operator()(size_t, cudaStream_t) const { return MRDFT_OK; }
 };
+struct NoFork {
+  mrdft_status operator()(bool) const { return MRDFT_OK; }
+};
 // before(j, s) runs before segment j's chain is enqueued on s, after(j, s)
 // after it; forked(parallel) runs once the worker streams have forked from
 // the caller's stream (parallel) or, without workers, before the first segment
-template <class F, class A, class B, class K>
-mrdft_status run_segments(mrdft_plan_s* p, cudaStream_t st, F&& chain, A&& after, B&& before, K&& forked) {
+template <class F, class A = NoAfter, class B = NoAfter, class K = NoFork>
+mrdft_status run_segments(mrdft_plan_s* p, cudaStream_t st, F&& chain, A&& after = NoAfter{}, B&& before = NoAfter{},
+                          K&& forked = NoFork{}) {
   const int nw = p->timing_serial ? 0 : (int)p->workers.size();
   if (nw <= 1) {
     mrdft_status r0 = forked(false);
