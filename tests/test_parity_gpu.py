@@ -258,7 +258,7 @@ def test_forward_host_entry(oracle):
     np.testing.assert_array_equal(y_host, run_forward(plan, x.reshape(-1)))
 
 
-@pytest.mark.parametrize("case", ["phases", "tile_split", "bitrev", "many_runs"])
+@pytest.mark.parametrize("case", ["phases", "tile_split", "bitrev", "many_runs", "lone"])
 def test_forward_host_overlapped_copies(oracle, case):
     """mrdft_forward_host copies each finished part of the output (the in-tile
     levels after the tile launch, the segment levels after the segments, the
@@ -267,6 +267,8 @@ def test_forward_host_overlapped_copies(oracle, case):
     over repeated calls."""
     if case == "many_runs":
         lengths = [1 << int(m) for m in np.random.default_rng(5).integers(3, 15, size=100)]
+    elif case == "lone":  # one small signal: one CTA per level, copied after that launch
+        lengths = [1 << 12]
     else:
         lengths = [1 << 20, 1 << 17, 1 << 13, 1 << 5, 1 << 3]
     opts = {"tile_split": 2} if case == "tile_split" else {}
