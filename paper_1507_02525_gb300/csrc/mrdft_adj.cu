@@ -231,7 +231,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     auto sink = [&](int, int b, int n, float2 v) MRDFT_INL {
       const float2 c = cmulc(conjf2(v), twq_l(tw, i, n));  // conj(w^n) zb[n]
       const int base = b << i;
-      const int i0 = pad16(base + n), i1 = pad16(base + h + n);
+      const int i0 = pad16(base + n), i1 = h >= 32 ? i0 + pad16(h) : pad16(base + h + n);
       ACC[i0] = cadd(ACC[i0], c);
       ACC[i1] = csub(ACC[i1], c);
     };

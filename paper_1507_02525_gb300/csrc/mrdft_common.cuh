@@ -137,10 +137,13 @@ __device__ __forceinline__ void idft_reg(float2 (&v)[R]) {
 // lanes walking rows with any power-of-two stride up to 64 rows, or walking
 // consecutive elements, hit distinct banks.  Index in float2 units; pairs
 // (2q, 2q+1) stay adjacent, so 16-byte vector accesses remain valid.
-__device__ __forceinline__ int swz128(int e) {
+__host__ __device__ __forceinline__ constexpr int swz128(int e) {
   const int r = e >> 4;
   return (r << 4) | ((((e >> 1) & 7) ^ ((r ^ (r >> 3) ^ (r >> 6)) & 7)) << 1) | (e & 1);
 }
+// swz128 is linear over XOR: for indices whose set bits do not overlap,
+// swz128(a + b) = swz128(a) ^ swz128(b), so offsets known at compile time
+// cost one XOR.
 // FFT work buffers: XOR the low 4 index bits with bits 4..7 and 8..11 so that
 // power-of-two strides up to 2^12 spread over all banks (8-byte elements).
 __device__ __forceinline__ int swzf(int e) { return e ^ (((e >> 4) ^ (e >> 8)) & 15); }

@@ -232,10 +232,15 @@ __global__ void __launch_bounds__(NT, LEAN ? 3 : (NT <= 256 ? 2 : 1)) k_fwd_tile
       constexpr int LRB = (i - 1) - 3;
       if (tid < (Tn >> 4)) {
         const int base = (tid >> LRB) << i, g = tid & ((1 << LRB) - 1);
+        // pad16 adds 2 per 32 elements: offsets of whole 32-element blocks
+        // (kk 2^LRB with LRB >= 5, and h >= 32) add their padded value
+        const int p0 = pad16(base + g);
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
           const int k = g + (kk << LRB);
-          ev[kk] = cadd(B[pad16(base + k)], B[pad16(base + h + k)]);  // U: child sum
+          const int pa = LRB >= 5 ? p0 + pad16(kk << LRB) : pad16(base + k);
+          const int pb = h >= 32 ? pa + pad16(h) : pad16(base + h + k);
+          ev[kk] = cadd(B[pa], B[pb]);  // U: child sum
         }
       }
     }
@@ -243,10 +248,14 @@ __global__ void __launch_bounds__(NT, LEAN ? 3 : (NT <= 256 ? 2 : 1)) k_fwd_tile
       constexpr int R = 1 << decltype(RBc)::value;
       const int base = b << i;
       const float2 w0 = twq_l(tw, i, n0);
+      // base, n0 < 2^LRB, r 2^LRB < h and h occupy disjoint bits: one swizzle
+      // per group, XORs for the rest
+      const int s0 = swz128(base + n0);
+      constexpr int sh = swz128(h);
       static_for<0, R>([&](auto RR) MRDFT_INL {
         constexpr int r = decltype(RR)::value;
-        const int n = n0 + (r << LRB);
-        v[r] = cmul_ct<2 * R, r>(cmul(csub(X[swz128(base + n)], X[swz128(base + h + n)]), w0));
+        const int sa = s0 ^ swz128(r << LRB);
+        v[r] = cmul_ct<2 * R, r>(cmul(csub(X[sa], X[sa ^ sh]), w0));
       });
     };
     auto pre = [&](int slot, int b, int k) MRDFT_INL {
