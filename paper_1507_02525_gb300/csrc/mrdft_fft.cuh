@@ -186,6 +186,9 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
         }
       } else {
         const int a0 = SEQ_MINOR ? (((g << RB) << nseq_log) + b) : ((b << LB) + (g << RB));
+        // zlay is linear over XOR and the element offsets occupy bits a0
+        // leaves clear: one layout computation per group
+        const int z0 = zlay<ZS>(a0);
         if constexpr (!SEQ_MINOR && ZS == 0 && R == 8) {
           // 8 consecutive elements = chunks c0 .. c0 + 3 of row a0 >> 4 (c0 = 0 or 4)
           const float2* rowp = Z + ((a0 >> 4) << 4);
@@ -198,7 +201,7 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
           }
         } else {
 #pragma unroll
-          for (int r = 0; r < R; ++r) v[j][r] = Z[zlay<ZS>(a0 + (SEQ_MINOR ? (r << nseq_log) : r))];
+          for (int r = 0; r < R; ++r) v[j][r] = Z[z0 ^ zlay<ZS>(SEQ_MINOR ? (r << nseq_log) : r)];
         }
       }
       const int tg = g >> SH;
@@ -247,8 +250,9 @@ __device__ __forceinline__ void cg_pass(float2* __restrict__ Z, int LB, int nseq
       }
     } else {
       const int a0 = SEQ_MINOR ? ((g << nseq_log) + b) : ((b << LB) + g);
+      const int z0 = zlay<ZS>(a0);  // as for the loads: offsets k 2^LRB lie above g's bits
 #pragma unroll
-      for (int k = 0; k < R; ++k) Z[zlay<ZS>(a0 + (SEQ_MINOR ? ((k << LRB) << nseq_log) : (k << LRB)))] = v[j][k];
+      for (int k = 0; k < R; ++k) Z[z0 ^ zlay<ZS>(SEQ_MINOR ? ((k << LRB) << nseq_log) : (k << LRB))] = v[j][k];
     }
   }
 }
