@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     }
     __syncthreads();
     if constexpr (i > 5) load_level(i - 1);
-    auto src = [&](int b, int n) MRDFT_INL -> float2 { return Z[stg<SA, 0>((b << (i - 1)) + n)]; };
+    const StgGroup<SA, 0> src{Z, 0, i - 1};
     auto sink = [&](int, int b, int n, float2 v) MRDFT_INL {
       const float2 c = cmulc(conjf2(v), twq_l(tw, i, n));  // conj(w^n) zb[n]
       const int base = b << i;
@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
       ACC[i0] = cadd(ACC[i0], c);
       ACC[i1] = csub(ACC[i1], c);
     };
-    cg_fft<i - 1, i - 1, NT, 8, false, false>(Z, i - 1, tn_log - i, tw, src, NoPre{}, sink);
+    cg_fft<i - 1, i - 1, NT, 8, false, kPreNone, 0, true>(Z, i - 1, tn_log - i, tw, src, NoPre{}, sink);
     __syncthreads();
   });
 
@@ -424,7 +424,7 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) 
   }
   __syncthreads();
   const TwQ tw{TQ, 13};
-  auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[stg<SA, SB>(n)]; };
+  const StgGroup<SA, SB> src{Z, 0, 0};
   float2 oa[PTS], ob[PTS];
   auto pre = [&](int slot, int, int n) MRDFT_INL {
     if (add) {
@@ -449,7 +449,7 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_adj_window(const AdjArgs a) 
       __stcg(acc + h + n, make_float2(-c.x, -c.y));
     }
   };
-  cg_fft<LB, LB, NT, PTS, false, kPreGroup>(Z, LB, 0, tw, src, pre, sink);
+  cg_fft<LB, LB, NT, PTS, false, kPreGroup, 0, true>(Z, LB, 0, tw, src, pre, sink);
   loss_flush<FUSED>(a, lsum);
 }
 
@@ -553,14 +553,14 @@ __global__ void __launch_bounds__(NT, E <= kPassElemsLog ? 2 : 1) k_adj_rows(con
   __syncthreads();
   const TwQ tw{TQ, CB};
   float2* U = a.scratch + sd.aux_off + (w << HB);
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[stg<SA, SB>((b << CB) + n)]; };
+  const StgGroup<SA, SB> src{S, 0, CB};
   // the intermediate is read by the cols pass right after: keep it in L2
   const uint64_t keep = l2_evict_last_policy();
   auto sink = [&](int, int b, int r, float2 v) MRDFT_INL {
     const float2 t = cmul(TWL[b * 65 + (r & 63)], TWH[b * (HU + 16 / KC) + (r >> 6)]);
     st_l2_keep(U + ((int64_t)(k0 + b) << CB) + r, cmulc(conjf2(v), t), keep);
   };
-  cg_fft<CB, CB, NT, PTS, false, kPreNone>(S, CB, KCB, tw, src, NoPre{}, sink);
+  cg_fft<CB, CB, NT, PTS, false, kPreNone, 0, true>(S, CB, KCB, tw, src, NoPre{}, sink);
   loss_flush<FUSED>(a, lsum);
 }
 
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_adj_cols(cons
     for (int l = threadIdx.x; l < (RC / 16) << QB; l += NT)
       discard_l2(U + ((int64_t)(l >> (RCB - 4)) << CB) + r0 + 16 * (l & ((RC / 16) - 1)));
   const TwQ tw{TQ, 12};
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[stg<6, 0>((n << RCB) + b)]; };
+  const StgGroup<6, 0> src{S, RCB, 0};
   float2 oa[PTS], ob[PTS];
   // the accumulated gradient at n and h + n, read once per group of 8 outputs
   auto pre = [&](int slot, int b, int q) MRDFT_INL {
@@ -644,7 +644,7 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_adj_cols(cons
       __stcg(acc + h + n, make_float2(-c.x, -c.y));
     }
   };
-  cg_fft<QB, QB, NT, PTS, true, kPreHalf, (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, pre, sink);
+  cg_fft<QB, QB, NT, PTS, true, kPreHalf, (RCB < 4 ? RCB : 4), true>(S, QB, RCB, tw, src, pre, sink);
 }
 
 // Two levels, one update of the accumulated gradient: the cols passes of
@@ -722,14 +722,14 @@ __global__ void __launch_bounds__(kColsThreads, 2) k_adj_cols2(const AdjArgs a) 
   }
   const TwQ tw{TQ, 12};
   // level i + 1: zb' per column, c1 back into Z1 in natural order
-  auto src1 = [&](int b, int n) MRDFT_INL -> float2 { return Z1[stg<SA1, 0>((n << RCB) + b)]; };
+  const StgGroup<SA1, 0> src1{Z1, RCB, 0};
   auto sink1 = [&](int, int b, int q, float2 v) MRDFT_INL {
     Z1[(q << RCB) + b] = cmulc(conjf2(v), cmul(ZC1[b], twq_l(tw, QB + 2, q)));
   };
-  cg_fft<QB + 1, QB + 1, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4)>(Z1, QB + 1, RCB, tw, src1, NoPre{}, sink1);
+  cg_fft<QB + 1, QB + 1, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4), true>(Z1, QB + 1, RCB, tw, src1, NoPre{}, sink1);
   __syncthreads();
   // level i: zb_c per (child, column), combined with c1 into the four rows
-  auto src0 = [&](int s, int n) MRDFT_INL -> float2 { return Z0[stg<3, 0>((n << (RCB + 1)) + s)]; };
+  const StgGroup<3, 0> src0{Z0, RCB + 1, 0};
   float2 oa[PTS], ob[PTS];
   auto pre0 = [&](int slot, int s, int q) MRDFT_INL {
     if (add) {
@@ -756,7 +756,7 @@ __global__ void __launch_bounds__(kColsThreads, 2) k_adj_cols2(const AdjArgs a) 
     __stcg(acc + n, ca);
     __stcg(acc + n + ((int64_t)Q << CB), cb);
   };
-  cg_fft<QB, QB, NT, PTS, true, kPreHalf, (RCB + 1 < 4 ? RCB + 1 : 4)>(Z0, QB, RCB + 1, tw, src0, pre0, sink0);
+  cg_fft<QB, QB, NT, PTS, true, kPreHalf, (RCB + 1 < 4 ? RCB + 1 : 4), true>(Z0, QB, RCB + 1, tw, src0, pre0, sink0);
 }
 
 constexpr size_t adj_cols2_smem() {

@@ -137,6 +137,23 @@ __device__ __forceinline__ int drev8(int v, int d) {
   return r;
 }
 
+// First-pass group source over input staged in the stg<A, B> layout at index
+// (n << ns) | (b << bs) (n and b in disjoint bit fields): the R inputs
+// n0 + r 2^LRB of a group share one layout computation and take an XOR each
+// (stg is linear over XOR, and r 2^LRB lies above n0 < 2^LRB).
+template <int A, int B>
+struct StgGroup {
+  const float2* S;
+  int ns, bs;
+  template <class V, class RBc>
+  __device__ __forceinline__ void operator()(int b, int n0, int LRB, V& v, RBc) const {
+    constexpr int R = 1 << RBc::value;
+    const int e0 = stg<A, B>((n0 << ns) | (b << bs));
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = S[e0 ^ stg<A, B>((r << LRB) << ns)];
+  }
+};
+
 // One pass of the constant-geometry DIT FFT.
 //   LB: log2 sequence length; nseq_log: log2 number of sequences;
 //   RB: log2 radix of this pass; SH: 3 * (DIF pass index) -- the twiddle of

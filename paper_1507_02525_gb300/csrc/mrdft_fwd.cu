@@ -423,7 +423,7 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_fwd_window(const FwdArgs a) 
   __syncthreads();
   const bool reread = sd.m > i;  // children of the next level: keep in L2
   float2 ea[PTS], eb[PTS];
-  auto src = [&](int, int n) MRDFT_INL -> float2 { return Z[stg<SA, SB>(n)]; };
+  const StgGroup<SA, SB> src{Z, 0, 0};
   auto pre = [&](int slot, int, int k) MRDFT_INL {
     ea[slot] = __ldcs(yprev + k);
     eb[slot] = __ldcs(yprev + h + k);
@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(kWinThreads, 2) k_fwd_window(const FwdArgs a) 
     if (reread) __stcg(dst, v);
     else __stcs(dst, v);
   };
-  cg_fft<LB, LB, NT, PTS, false, kPreGroup>(Z, LB, 0, tw, src, pre, sink);
+  cg_fft<LB, LB, NT, PTS, false, kPreGroup, 0, true>(Z, LB, 0, tw, src, pre, sink);
 }
 
 // cols pass: work area 2^E, w_{2^12} table, chunk twiddles (RC <= 2^(E-3))
@@ -523,12 +523,12 @@ __global__ void __launch_bounds__(NT, E < kPassElemsLog ? 4 : 2) k_fwd_cols(cons
   }
   __syncthreads();
   float2* F = a.scratch + sd.aux_off + ((int64_t)it.window << HB);
-  auto src = [&](int b, int n) MRDFT_INL -> float2 { return S[stg<6, 0>((n << RCB) + b)]; };
+  const StgGroup<6, 0> src{S, RCB, 0};
   // the intermediate is read by the rows pass right after: keep it in L2
   // (f_late: the rows pass comes much later; let it leave L2 first instead)
   const uint64_t keep = a.f_late ? l2_evict_first_policy() : l2_evict_last_policy();
   auto sink = [&](int, int b, int k2, float2 v) MRDFT_INL { st_l2_keep(F + ((int64_t)k2 << CB) + r0 + b, v, keep); };
-  cg_fft<QB, QB, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4)>(S, QB, RCB, tw, src, NoPre{}, sink);
+  cg_fft<QB, QB, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4), true>(S, QB, RCB, tw, src, NoPre{}, sink);
 }
 
 // Two levels, one read of x: the cols passes of levels i and i + 1 (the same
@@ -599,17 +599,17 @@ __global__ void __launch_bounds__(kColsThreads, 2) k_fwd_cols2(const FwdArgs a) 
   const uint64_t keep = l2_evict_last_policy();
   // level i + 1 (window it.window, h = 2^i): intermediate F1[k2][r]
   float2* F1 = a.scratch2 + sd.aux_off + ((int64_t)it.window << i);
-  auto src1 = [&](int b, int n) MRDFT_INL -> float2 { return Z1[stg<SA1, 0>((n << RCB) + b)]; };
+  const StgGroup<SA1, 0> src1{Z1, RCB, 0};
   auto sink1 = [&](int, int b, int k2, float2 v) MRDFT_INL { st_l2_keep(F1 + ((int64_t)k2 << CB) + r0 + b, v, keep); };
-  cg_fft<QB + 1, QB + 1, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4)>(Z1, QB + 1, RCB, tw, src1, NoPre{}, sink1);
+  cg_fft<QB + 1, QB + 1, NT, PTS, true, kPreNone, (RCB < 4 ? RCB : 4), true>(Z1, QB + 1, RCB, tw, src1, NoPre{}, sink1);
   // level i (children 2W, 2W + 1, h = 2^(i-1)): sequence s = c RC + b
   float2* F0 = a.scratch + sd.aux_off + ((int64_t)(2 * it.window) << (i - 1));
-  auto src0 = [&](int s, int n) MRDFT_INL -> float2 { return Z0[stg<3, 0>((n << (RCB + 1)) + s)]; };
+  const StgGroup<3, 0> src0{Z0, RCB + 1, 0};
   auto sink0 = [&](int, int s, int k2, float2 v) MRDFT_INL {
     const int c = s >> RCB, b = s & (RC - 1);
     st_l2_keep(F0 + ((int64_t)c << (i - 1)) + ((int64_t)k2 << CB) + r0 + b, v, keep);
   };
-  cg_fft<QB, QB, NT, PTS, true, kPreNone, (RCB + 1 < 4 ? RCB + 1 : 4)>(Z0, QB, RCB + 1, tw, src0, NoPre{}, sink0);
+  cg_fft<QB, QB, NT, PTS, true, kPreNone, (RCB + 1 < 4 ? RCB + 1 : 4), true>(Z0, QB, RCB + 1, tw, src0, NoPre{}, sink0);
 }
 
 constexpr size_t cols2_smem() {
