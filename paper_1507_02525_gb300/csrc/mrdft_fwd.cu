@@ -698,10 +698,11 @@ __global__ void __launch_bounds__(NT, PF ? (E < kPassElemsLog ? 2 : 1) : (E < kP
   auto src = [&](int b, int n0, int LRB, auto& v, auto RBc) MRDFT_INL {
     constexpr int R = 1 << decltype(RBc)::value;
     const float2 lo = TWL[b * 65 + (n0 & 63)];
+    const int e0 = stg<SA, SB>((n0 << KCB) | b);  // stg is linear over XOR: one layout computation per group
 #pragma unroll
     for (int j = 0; j < R; ++j) {
       const int n = n0 + (j << LRB);
-      v[j] = cmul(S[stg<SA, SB>((n << KCB) + b)], cmul(lo, TWH[b * (HU + 16 / KC) + (n >> 6)]));
+      v[j] = cmul(S[e0 ^ stg<SA, SB>((j << LRB) << KCB)], cmul(lo, TWH[b * (HU + 16 / KC) + (n >> 6)]));
     }
   };
   const bool reread = sd.m > i;
