@@ -205,25 +205,32 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 2 : 1) k_adj_tile(const AdjArg
     constexpr int SA = i <= 10 ? 3 : 6;  // staging layout of the odd half
     const float2* Ein = E[(i + 1) & 1];
     float2* Eout = E[i & 1];
-    // G_i = g_i + P_i: even half -> Eout, conj(odd half) -> Z
+    // G_i = g_i + P_i: even half -> Eout, conj(odd half) -> Z.  Pair c (bins
+    // e = 2c, e + 1) of window w = e >> i, bin k = e mod 2^i has its half-bin
+    // index w h + k / 2 = c, and its parent's even bins at pb(e) = e with bit
+    // i deleted; both maps and both layouts are linear over XOR and
+    // c = tid + q NT splits into disjoint bit fields, so each index is a
+    // per-thread base XOR a constant per q
+    auto pbf = [&](int e) MRDFT_INL { return ((e >> (i + 1)) << i) | (e & (L - 1)); };
+    const int eb0 = swzf(pbf(tid << 1)), eo0 = swzf(tid), z0 = stg<SA, 0>(tid);
 #pragma unroll
     for (int q = 0; q < ITER; ++q) {
       const int c = tid + q * NT;
       if (c >= (Tn >> 1)) continue;
       const int e = c << 1;
       const float4 g = gv[q];
-      const int w = e >> i, k = e & (L - 1);
       float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
       if (i == tl) {
         if (below)
-          p = __ldcg(reinterpret_cast<const float4*>(a.e_in + sd0.aux_off + ((int64_t)(it.tile >> 1) << tl) + k));
+          p = __ldcg(reinterpret_cast<const float4*>(a.e_in + sd0.aux_off + ((int64_t)(it.tile >> 1) << tl) +
+                                                     (e & (L - 1))));
       } else {
-        const int pb = ((w >> 1) << i) + k;
-        const float2 pe = Ein[swzf(pb)], po = Ein[swzf(pb + 1)];
+        const int ib = eb0 ^ swzf(pbf((q * NT) << 1));  // pb is even: its pair partner is ib ^ 1
+        const float2 pe = Ein[ib], po = Ein[ib ^ 1];
         p = make_float4(pe.x, pe.y, po.x, po.y);
       }
-      Eout[swzf(w * h + (k >> 1))] = make_float2(g.x + p.x, g.y + p.y);
-      Z[stg<SA, 0>(w * h + (k >> 1))] = make_float2(g.z + p.z, -(g.w + p.w));
+      Eout[eo0 ^ swzf(q * NT)] = make_float2(g.x + p.x, g.y + p.y);
+      Z[z0 ^ stg<SA, 0>(q * NT)] = make_float2(g.z + p.z, -(g.w + p.w));
     }
     __syncthreads();
     if constexpr (i > 5) load_level(i - 1);

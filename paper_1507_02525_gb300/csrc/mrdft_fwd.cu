@@ -264,10 +264,16 @@ __global__ void __launch_bounds__(NT, LEAN ? 3 : (NT <= 256 ? 2 : 1)) k_fwd_tile
         ev[slot] = cadd(B[pad16(base + k)], B[pad16(base + h + k)]);  // U: child sum
       }
     };
-    auto sink = [&](int slot, int b, int k, float2 odd) MRDFT_INL {
-      const int e = (b << i) + 2 * k;
+    // the last pass gives this thread group G = tid: window tid >> LRB, bins
+    // g + slot 2^LRB (g = tid mod 2^LRB), pair index e = eL + slot 2^(LRB+1);
+    // pad16 adds whole 32-element blocks once 2^(LRB+1) >= 32
+    constexpr int LRBl = (i - 1) - 3;
+    const int eL = ((tid >> LRBl) << i) + 2 * (tid & ((1 << LRBl) - 1));
+    const int pL = pad16(eL);
+    auto sink = [&](int slot, int, int, float2 odd) MRDFT_INL {
+      const int e = eL + (slot << (LRBl + 1));
       const float4 v = make_float4(ev[slot].x, ev[slot].y, odd.x, odd.y);
-      if (keep) st4s(B + pad16(e), v);
+      if (keep) st4s(B + (LRBl >= 4 ? pL + pad16(slot << (LRBl + 1)) : pad16(e)), v);
       float4* dst;
       if (single) {
         dst = reinterpret_cast<float4*>(ylev + e);
